@@ -1,0 +1,372 @@
+"""Benchmark of the ADG hot path on GB300: GDoF-RK-stages/s.
+
+Workload (default): 2D isentropic vortex, periodic [-5,5]^2, 256^2 quads, degree 4
+(5x5 Gauss points), 8x8 subdomains of 32x32 elements, communication-avoiding schedule with
+L = 3 and the AT flux (N_p + 1 = 5 stored levels), CK4(5) low-storage RK, CFL 0.1, FP64.
+One benchmark step is one full schedule cycle: L + N_p + 1 = 8 time steps (5 communication
+steps, 3 delayed ones), i.e. 40 RK stages over 6,553,600 DoF.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--precision fp64]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank runs an independent
+replica on its own GPU ("replicas only": the path has no exchange between GPUs).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GDoF-RK-stages/s"
+N_ELEM, DEGREE, P, L = 256, 4, 8, 3
+CFL = 0.1
+
+
+def workload_config(precision):
+    return {"workload": f"2D isentropic vortex 256^2 quads p=4, 8x8 subdomains, CAA L=3, AT flux "
+                        f"(5 levels), CK4(5), CFL 0.1, operator {precision}",
+            "n_elem": [N_ELEM, N_ELEM], "degree": DEGREE, "subdomains": [P, P], "max_delay": L,
+            "flux": "at", "rk": "ck45", "precision": precision,
+            "time_steps_per_step": L + DEGREE + 1, "rk_stages": 5,
+            "n_dof": 4 * N_ELEM * N_ELEM * (DEGREE + 1) ** 2,
+            "l2_policy": "L2 flushed (256 MiB write) between timed steps",
+            "parallelism": "replicas"}
+
+
+# ---- algorithmic work per DoF and RK stage -------------------------------------------
+def vol_flops_per_node(D=2, N=DEGREE + 1):
+    """Flops of the volume/update kernel per node (FMA = 2): pointwise Euler flux,
+    sum-factorised derivative along D directions, face lift, 2N RK update, next traces."""
+    NV = D + 2
+    pointwise = 1 + D + 2 * D + 3 + 1 + D * (D + 2)
+    sweeps = 2 * D * N * NV
+    lift = 4 * D * NV
+    rk = 5 * NV
+    traces = 4 * D * NV
+    return pointwise + sweeps + lift + rk + traces
+
+
+def vol_bytes_per_dof_stage(stage, stages=5):
+    """Algorithmic HBM bytes per DoF of one 2N stage: read w (+ q after the first stage),
+    write w (+ q before the last stage), FP64."""
+    b = 16
+    if stage > 0:
+        b += 8
+    if stage < stages - 1:
+        b += 8
+    return b
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(os.path.join(ROOT, "paper_2603_28710_gb300", "csrc"))):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(ROOT, "paper_2603_28710_gb300", "csrc", name), "rb") as f:
+                h.update(name.encode())
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(precision):
+    """DRAM bytes per launch of the volume kernel from the committed ncu summary, if it was
+    taken on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", f"vol_kernel_traffic_{precision}.txt")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if "=" in line and not line.startswith("#"):
+            k, v = line.split("=", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("source_hash") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# ---- clocks sampled during the timed region -------------------------------------------
+class ClockSampler:
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---- oracle CPU baseline ---------------------------------------------------------------
+def oracle_sample(time_steps):
+    """Times the CPU oracle on the full-size workload for a few time steps; returns
+    (GDoF-RK-stages/s, seconds)."""
+    import oracle
+    o = oracle.Oracle(n_elem=(N_ELEM, N_ELEM), degree=DEGREE, P=(P, P), max_delay=L, flux="at",
+                      rk="ck45", dt=1.0)
+    u0 = o.init_vortex()
+    dt = o.dt_from_cfl(u0, CFL, 0.0)
+    o = oracle.Oracle(n_elem=(N_ELEM, N_ELEM), degree=DEGREE, P=(P, P), max_delay=L, flux="at",
+                      rk="ck45", dt=dt)
+    o.set_state(u0)
+    t0 = time.perf_counter()
+    o.step(time_steps)
+    sec = time.perf_counter() - t0
+    ndof = 4 * N_ELEM * N_ELEM * (DEGREE + 1) ** 2
+    return ndof * 5 * time_steps / sec / 1e9, sec
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    per = []
+    for _ in range(args.warmup):
+        oracle_sample(1)
+    for _ in range(args.steps):
+        v, sec = oracle_sample(1)
+        per.append(sec)
+    total = sum(per)
+    ndof = 4 * N_ELEM * N_ELEM * (DEGREE + 1) ** 2
+    value = ndof * 5 * args.steps / total / 1e9
+    line = {"metric": METRIC, "value": value, "unit": METRIC, "impl": "reference", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config("fp64"),
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
+                             "sample": "one RK time step (5 stages) of the full 256^2 p=4 "
+                                       "workload per step, single-threaded C oracle"},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---- GPU arm -----------------------------------------------------------------------------
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    from paper_2603_28710_gb300 import adg, build
+
+    if rank == 0 or not os.path.exists(adg.LIB_PATH):
+        build.build()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    steps_per = L + DEGREE + 1
+    ndof = 4 * N_ELEM * N_ELEM * (DEGREE + 1) ** 2
+    work = ndof * 5 * steps_per  # DoF-stages per benchmark step
+
+    s = adg.Solver(n_elem=(N_ELEM, N_ELEM), degree=DEGREE, P=(P, P), max_delay=L, flux="at",
+                   rk="ck45", cfl=CFL, precision=args.precision, stream=stream.cuda_stream)
+    s.init_vortex()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        s.step(steps_per)
+    torch.cuda.synchronize()
+
+    # device-timed region: K steps, L2 flushed between them (outside the events)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    gpu_idx = os.environ.get("CUDA_VISIBLE_DEVICES", str(local_rank)).split(",")[local_rank] \
+        if os.environ.get("CUDA_VISIBLE_DEVICES") else str(local_rank)
+    barrier()
+    torch.cuda.synchronize()
+    s.set_profiling(True)
+    with ClockSampler(gpu_idx) as clk:
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            s.step(steps_per)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    prof = s.get_profile()
+    s.set_profiling(False)
+    ms_list = [a.elapsed_time(b) for a, b in ev]
+    ms = sum(ms_list)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * work * args.steps / (ms * 1e-3) / 1e9
+
+    # end to end through the public API: pinned host state in, 8 steps, state out
+    host_in = torch.from_numpy(s.get_state()).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    dt = s.info()["dt"]
+    s2 = adg.Solver(n_elem=(N_ELEM, N_ELEM), degree=DEGREE, P=(P, P), max_delay=L, flux="at",
+                    rk="ck45", dt=dt, precision=args.precision, stream=stream.cuda_stream)
+    for _ in range(2):
+        s2.set_state(host_in)
+        s2.step(steps_per)
+        s2.get_state(host_out)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        s2.set_state(host_in)
+        s2.step(steps_per)
+        s2.get_state(host_out)
+    torch.cuda.synchronize()
+    e2e_sec = time.perf_counter() - t0
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_sec], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_sec = float(t.item())
+    e2e_value = world * work * args.steps / e2e_sec / 1e9
+    state_bytes = ndof * 8
+
+    if rank != 0:
+        return
+
+    # roofline of the dominant kernel (volume/update kernel), timed live above
+    vol_ms, vol_n = prof["vol"]
+    flux_ms, flux_n = prof["flux"]
+    vol_avg_s = vol_ms * 1e-3 / max(vol_n, 1)
+    nodes = N_ELEM * N_ELEM * (DEGREE + 1) ** 2
+    flops_launch = vol_flops_per_node() * nodes
+    bytes_launch = np.mean([vol_bytes_per_dof_stage(m) for m in range(5)]) * ndof
+    pk = peaks()
+    fp64_peak_tflops = 1.25  # nominal GB300 FP64 rate (no FP64 tensor advantage)
+    if args.precision == "fp64":
+        roof = {"bound": "alu", "achieved": flops_launch / vol_avg_s / 1e12,
+                "peak": fp64_peak_tflops, "unit": "TFLOP/s",
+                "peak_source": "nominal FP64 1.25 TFLOP/s (recipe table); 1.19 measured by an FMA probe"}
+    else:
+        roof = {"bound": "hbm", "achieved": bytes_launch / vol_avg_s / 1e9,
+                "peak": pk.get("hbm_gbs", 6800.0), "unit": "GB/s",
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in pk else "fallback 6.8 TB/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["kernel"] = "vol_kernel<2,5>"
+    roof["traffic"] = ncu_traffic(args.precision)
+    roof["algorithmic_bytes_per_launch"] = bytes_launch
+    roof["algorithmic_flops_per_launch"] = flops_launch
+    roof["hbm_view"] = {"achieved_gbs": bytes_launch / vol_avg_s / 1e9,
+                        "peak_gbs": pk.get("hbm_gbs", 6800.0),
+                        "frac": bytes_launch / vol_avg_s / 1e9 / pk.get("hbm_gbs", 6800.0)}
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        v, sec = oracle_sample(args.cpu_steps)
+        cpu = {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle",
+               "sample": f"{args.cpu_steps} RK time steps (5 stages each) of the full 256^2 p=4 "
+                         f"workload, single-threaded C oracle, {sec:.1f} s"}
+
+    clocks = clk.summary()
+    line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "fp32": "f32", "df64": "f32x2"}[args.precision],
+            "data": "synthetic", "config": workload_config(args.precision),
+            "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": state_bytes,
+                    "d2h_bytes_per_step": state_bytes},
+            "roofline": roof, "cpu_baseline": cpu,
+            "clocks": clocks,
+            "gpu_launches": int(vol_n + flux_n),
+            "kernels": {"vol_kernel": {"ms_per_launch": vol_ms / max(vol_n, 1), "launches": vol_n},
+                        "flux_kernel": {"ms_per_launch": flux_ms / max(flux_n, 1),
+                                        "launches": flux_n}}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "df64"])
+    ap.add_argument("--cpu-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    try:
+        run_gpu(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

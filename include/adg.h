@@ -1,0 +1,209 @@
+/*
+ * adg.h -- C ABI of the GB300 (sm_103a) asynchronous discontinuous Galerkin operator.
+ *
+ * The library advances the compressible Euler equations (Section 2, Eq. 1-3, no source
+ * term) discretised by a nodal DG method on a periodic, uniform Cartesian quad/hex mesh
+ * (Section 2.1, Eq. 4-7) with the Rusanov flux of Eq. 8-9 and low-storage explicit
+ * Runge-Kutta time stepping (Section 2.3, Eq. 10, Table 2).  The asynchronous variants of
+ * Section 3 are emulated on one GPU: the mesh is cut into P[0] x P[1] (x P[2]) logical
+ * subdomains ("processing elements"); fluxes on faces between two subdomains use delayed
+ * data held in a device ring buffer of past time levels, refreshed on the schedule of
+ * Algorithm 2 (standard flux), Algorithm 3 (AT flux, Eq. 14-15) or a seeded random-delay
+ * schedule.  Interior faces always use current data.
+ *
+ * Discretisation details fixed by this library:
+ *   - nodes and quadrature: (degree+1)^dim Gauss-Legendre points per element, collocated;
+ *   - state layout (host and device): FP64, structure of arrays [var][element][node],
+ *       var     = rho, rho*u_x, rho*u_y, (rho*u_z), E               (dim+2 variables)
+ *       element = ex + n_elem[0] * (ey + n_elem[1] * ez)           (x fastest)
+ *       node    = a + (degree+1) * (b + (degree+1) * c)            (xi_x fastest),
+ *     node a in direction d sits at lo[d] + (ex + (xi_a + 1)/2) * h[d] with xi_a the a-th
+ *     Gauss-Legendre point on [-1, 1] in increasing order;
+ *   - the time step is constant for a run (the AT weights assume equally spaced levels).
+ *
+ * Conventions for every entry point:
+ *   - returns ADG_OK or an error status; no exception or abort crosses the ABI;
+ *     adg_last_error() gives a message for the last failing call on a handle (or, with a
+ *     NULL handle, for the last failing adg_create / host helper on this thread);
+ *   - caller buffers are read or written only during the call; the library keeps no
+ *     pointer to them.  "on_device" arguments say whether a pointer is a CUDA device
+ *     address (1) or host memory (0);
+ *   - a handle owns all device memory it allocates; handles are not thread-safe (use one
+ *     per thread); all device work is ordered on the handle's CUDA stream.
+ */
+#ifndef ADG_H
+#define ADG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct adg_solver adg_solver;
+
+typedef enum {
+  ADG_OK = 0,
+  ADG_ERR_INVALID = 1,     /* bad argument (size, range, NULL where not allowed)        */
+  ADG_ERR_UNSUPPORTED = 2, /* valid but not built (e.g. degree above the compiled range) */
+  ADG_ERR_CUDA = 3,        /* a CUDA runtime call failed; see adg_last_error             */
+  ADG_ERR_OOM = 4,         /* device allocation failed                                   */
+  ADG_ERR_NONFINITE = 5,   /* the state holds NaN or Inf (adg_check_finite)              */
+  ADG_ERR_TIMEOUT = 6,     /* reserved for bounded device-side waits                     */
+  ADG_ERR_STATE = 7        /* call out of order (e.g. adg_step before adg_set_state)      */
+} adg_status;
+
+/* How faces between two subdomains get their flux (Section 3). */
+typedef enum {
+  ADG_FLUX_SYNC = 0,        /* Algorithm 1: every face uses current data; P ignored       */
+  ADG_FLUX_STD_DELAYED = 1, /* Algorithm 2 / Eq. 13: reuse the stored flux of level n-k   */
+  ADG_FLUX_AT = 2,          /* Algorithm 3 / Eq. 14: AT combination of stored fluxes      */
+  ADG_FLUX_AT_TRACE = 3     /* AT extrapolation of both stored traces, then Eq. 8         */
+} adg_flux;
+
+typedef enum {
+  ADG_DELAY_CAA = 0,   /* Algorithm 2 (n % L == 0) or Algorithm 3 (n % (L+Np+1) < Np+1)   */
+  ADG_DELAY_RANDOM = 1 /* per step and subdomain interface: delay = splitmix64(seed ^
+                          (n * n_iface + iface)) % (random_delay_max + 1), reduced to 0
+                          while the history is shorter than the delay needs             */
+} adg_delay_mode;
+
+typedef enum {
+  ADG_RK_2R_22 = 0,  /* LSERK(2,2), Table 2, two-register form of Eq. 10              */
+  ADG_RK_2R_33 = 1,  /* LSERK(3,3), Table 2                                            */
+  ADG_RK_2N_CK45 = 2 /* Carpenter & Kennedy (1994) five-stage fourth-order 2N scheme
+                        (not printed in the paper)                                     */
+} adg_rk;
+
+typedef enum {
+  ADG_PREC_FP64 = 0,  /* operator in native FP64                                         */
+  ADG_PREC_FP32 = 1,  /* operator (traces, fluxes, volume terms) in FP32; the solution is
+                         still accumulated in FP64                                      */
+  ADG_PREC_DF64 = 2   /* operator in FP32-pair ("double-float") arithmetic, about 48
+                         significant bits; solution accumulated in FP64                 */
+} adg_precision;
+
+typedef struct {
+  int dim;          /* 2 or 3                                                          */
+  int n_elem[3];    /* elements per direction; entries beyond dim are ignored          */
+  double lo[3];     /* periodic box [lo, hi] per direction                             */
+  double hi[3];
+} adg_mesh;
+
+typedef struct {
+  adg_rk rk;                 /* default ADG_RK_2N_CK45                                  */
+  double dt;                 /* > 0: fixed time step; <= 0: from cfl at adg_set_state  */
+  double cfl;                /* dt = cfl h_min / ((2 degree + 1) max(|u| + c)), default 0.1 */
+  double t_end;              /* > 0: dt shortened so that a whole number of steps ends at t_end */
+  double gamma;              /* ratio of specific heats, default 1.4                   */
+  adg_delay_mode delay_mode; /* default ADG_DELAY_CAA                                  */
+  uint64_t seed;             /* random-delay seed                                      */
+  int random_delay_max;      /* 0..15, random mode only                                */
+  int at_np;                 /* AT stencil uses at_np+1 stored levels; <= 0: = degree  */
+  adg_precision precision;   /* default ADG_PREC_FP64                                  */
+  void* cuda_stream;         /* cudaStream_t to order work on; NULL: the library makes one */
+} adg_options;
+
+/* Fills *opt with the defaults listed above. */
+adg_status adg_default_options(adg_options* opt);
+
+/* Creates a solver (allocates every device buffer it will use).
+ *   mesh:      periodic uniform mesh; n_elem[d] >= 1 and divisible by P[d].
+ *   degree:    polynomial degree N_p, 1..7 in 2D and 1..5 in 3D.
+ *   P:         logical subdomains per direction (entries beyond dim ignored); P[d] = 1
+ *              gives no subdomain boundary across direction d (the periodic wrap face is
+ *              then interior).
+ *   max_delay: L of Algorithms 2/3: >= 1 for ADG_FLUX_STD_DELAYED, >= 0 for the AT modes;
+ *              ignored by ADG_FLUX_SYNC and by the random mode.
+ *   flux:      face rule on subdomain boundaries.
+ *   opt:       NULL for defaults.
+ * Errors: ADG_ERR_INVALID, ADG_ERR_UNSUPPORTED, ADG_ERR_OOM, ADG_ERR_CUDA.  *out is set
+ * to NULL on error. */
+adg_status adg_create(const adg_mesh* mesh, int degree, const int P[3], int max_delay,
+                      adg_flux flux, const adg_options* opt, adg_solver** out);
+
+/* Copies a state in (count must equal adg_info's n_dof) and restarts the schedule: the
+ * step counter and time go to 0, the delay history is emptied, and dt is derived from
+ * this state when options.dt <= 0.  Errors: ADG_ERR_INVALID (count, NULL), ADG_ERR_CUDA. */
+adg_status adg_set_state(adg_solver* s, const double* u, int64_t count, int on_device);
+
+/* Evaluates the initial condition at the nodes and sets it as the state (like
+ * adg_set_state).  Isentropic vortex (Section 5.1): strength beta, centre (x0, y0),
+ * background velocity (1, 0), nearest periodic image; in 3D it is extruded along z.   */
+adg_status adg_init_vortex(adg_solver* s, double t, double beta, double x0, double y0);
+/* Taylor-Green vortex on the box (rho0 = V0 = 1, p0 = 1/(gamma mach^2)); 3D only.      */
+adg_status adg_init_tgv(adg_solver* s, double mach);
+
+/* Advances n_steps time steps (each: all Runge-Kutta stages).  Work is enqueued on the
+ * handle's stream; the call returns without waiting for the GPU.
+ * Errors: ADG_ERR_STATE (no state set), ADG_ERR_INVALID (n_steps < 0), ADG_ERR_CUDA. */
+adg_status adg_step(adg_solver* s, int n_steps);
+
+/* Copies the current state out (waits for the stream).  count must equal n_dof. */
+adg_status adg_get_state(adg_solver* s, double* u, int64_t count, int on_device);
+
+/* Synchronous DG operator k = M^{-1} L_h(u) (Eq. 7; every face with current data) for an
+ * arbitrary state u of n_dof values, written to k (same layout).  Does not touch the
+ * solver's state or schedule.  Waits for the stream. */
+adg_status adg_rhs(adg_solver* s, const double* u, double* k, int64_t count, int on_device);
+
+/* Schedule of steps n0 .. n0+n-1 (integer data, computed on the host):
+ *   comm[i]: 1 when every subdomain face uses current data in step n0+i;
+ *   k[i]:    the delay counter of Algorithms 2/3 (random mode: the largest delay);
+ *   iface_delay (nullable) [n][n_iface]: the delay of each subdomain interface.
+ * Interface numbering: for each direction d with P[d] > 1 (in increasing d) one block of
+ * P[0]*P[1]*P[2] interfaces, indexed by the subdomain on the low side of the face. */
+adg_status adg_get_schedule(const adg_solver* s, int64_t n0, int n, int32_t* comm, int32_t* k,
+                            int32_t* iface_delay);
+
+/* Current time, step count, time step and number of degrees of freedom
+ * (n_dof = (dim+2) * n_elements * (degree+1)^dim).  Any pointer may be NULL. */
+adg_status adg_info(const adg_solver* s, double* t, int64_t* step, double* dt, int64_t* n_dof);
+
+/* Conserved totals sum_e sum_q omega_q |J| w_q for each variable (dim+2 values) of the
+ * current state; a deterministic reduction.  Waits for the stream. */
+adg_status adg_conservation(adg_solver* s, double* sums);
+
+/* Absolute L2 errors (density, momentum vector, energy) of the current state against the
+ * exact isentropic vortex at time t, with (degree+2)^dim Gauss points per element.      */
+adg_status adg_l2_error_vortex(adg_solver* s, double t, double beta, double x0, double y0,
+                               double* err3);
+
+/* ADG_OK if every state value is finite, ADG_ERR_NONFINITE otherwise. */
+adg_status adg_check_finite(adg_solver* s);
+
+/* Kernel timing.  While enabled, adg_step records a CUDA event pair on the handle's stream
+ * around every kernel it launches.  adg_get_profile waits for the stream and returns, per
+ * kernel kind (0: face-flux kernel, 1: volume/update kernel), the summed device time in ms
+ * and the launch count since profiling was enabled or last read; it then resets them. */
+adg_status adg_set_profiling(adg_solver* s, int enable);
+adg_status adg_get_profile(adg_solver* s, double* ms, int64_t* launches);
+
+/* Message for the last failing call on s (NULL: on this thread, for calls without a
+ * handle).  Valid until the next call on the same handle/thread. */
+const char* adg_last_error(const adg_solver* s);
+
+/* Frees the handle and its device memory.  NULL-safe. */
+void adg_destroy(adg_solver* s);
+
+/* ---- host-only helpers (no GPU needed) ---------------------------------------------- */
+
+/* Gauss-Legendre nodes x[n] (increasing) and weights w[n] on [-1, 1], 1 <= n <= 8. */
+adg_status adg_host_gauss(int n, double* x, double* w);
+/* AT weights of Eq. 14 for delay k_m (fractional allowed): c[0..np] on levels
+ * n-k_m, ..., n-k_m-np, from the moment conditions of Eq. 15 with r = 1. */
+adg_status adg_host_at_coeffs(int np, double km, double* c);
+/* Low-storage coefficients of a scheme: a[s], b[s], stage abscissae c[s]; returns the
+ * stage count in *stages.  2R: a = (a_1..a_{s-1}, 0), b as in Table 2.  2N: A_i, B_i.  */
+adg_status adg_host_rk(adg_rk scheme, int* stages, double* a, double* b, double* c);
+/* Same schedule as adg_get_schedule without a solver (dim, P[3] as in adg_create). */
+adg_status adg_host_schedule(adg_flux flux, adg_delay_mode mode, int max_delay, int np, int dim,
+                             const int P[3], uint64_t seed, int random_delay_max, int64_t n0,
+                             int n, int32_t* comm, int32_t* k, int32_t* iface_delay);
+/* Number of subdomain interfaces (see adg_get_schedule). */
+int adg_host_num_interfaces(int dim, const int P[3]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ADG_H */

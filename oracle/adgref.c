@@ -127,18 +127,49 @@ static void lu_solve(int m, const double* LU, const int* piv, double* b) {
 /* dt cancels; k_m may be fractional (naive RK coupling, k_m = k + stage offset).        */
 /* ------------------------------------------------------------------------------------ */
 int adgref_at_coeffs(int np, double km, double* c) {
+  /* The moment matrix is a Vandermonde matrix in -(k_m + l); for N_p >= 4 its condition
+     number exceeds 1e6, so Gaussian elimination with partial pivoting is carried out in
+     long double to keep the weights accurate to FP64 rounding. */
   int m = np + 1;
   if (np < 0 || m > 16) return -1;
-  double A[256];
-  int piv[16];
+  long double A[256], b[16];
   for (int z = 0; z < m; ++z) {
-    double fact = 1.0;
+    long double fact = 1.0L;
     for (int q = 2; q <= z; ++q) fact *= q;
-    for (int l = 0; l < m; ++l) A[z * m + l] = pow(-(km + l), z) / fact;
-    c[z] = (z == 0) ? 1.0 : 0.0;
+    for (int l = 0; l < m; ++l) {
+      long double p = 1.0L;
+      for (int q = 0; q < z; ++q) p *= -((long double)km + l);
+      A[z * m + l] = p / fact;
+    }
+    b[z] = (z == 0) ? 1.0L : 0.0L;
   }
-  if (lu_factor(m, A, piv)) return -1;
-  lu_solve(m, A, piv, c);
+  for (int col = 0; col < m; ++col) {
+    int best = col;
+    for (int r = col + 1; r < m; ++r)
+      if (fabsl(A[r * m + col]) > fabsl(A[best * m + col])) best = r;
+    if (A[best * m + col] == 0.0L) return -1;
+    if (best != col) {
+      for (int j = 0; j < m; ++j) {
+        long double t = A[col * m + j];
+        A[col * m + j] = A[best * m + j];
+        A[best * m + j] = t;
+      }
+      long double t = b[col];
+      b[col] = b[best];
+      b[best] = t;
+    }
+    for (int r = col + 1; r < m; ++r) {
+      long double f = A[r * m + col] / A[col * m + col];
+      for (int j = col; j < m; ++j) A[r * m + j] -= f * A[col * m + j];
+      b[r] -= f * b[col];
+    }
+  }
+  for (int r = m - 1; r >= 0; --r) {
+    long double acc = b[r];
+    for (int j = r + 1; j < m; ++j) acc -= A[r * m + j] * b[j];
+    b[r] = acc / A[r * m + r];
+  }
+  for (int l = 0; l < m; ++l) c[l] = (double)b[l];
   return 0;
 }
 

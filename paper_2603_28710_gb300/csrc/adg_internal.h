@@ -1,0 +1,109 @@
+// Internal declarations shared by the host side and the kernels of the ADG library.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace adg {
+
+constexpr int kMaxN = 8;        // nodes per direction (degree <= 7)
+constexpr int kMaxN3D = 6;      // 3D builds degree <= 5
+constexpr int kMaxRing = 24;    // ring levels (random_delay_max + np + 1 <= 15 + 7 + 1)
+constexpr int kMaxCoefDelay = 16;
+
+// Operator tables in FP64; kernels convert entries to their arithmetic type.
+struct OpTables {
+  double Q[3][kMaxN * kMaxN];  // (2/h_d) omega_a l_i'(xi_a) / omega_i, entry [i*N + a]
+  double Lp[3][kMaxN];         // (2/h_d) l_i(+1) / omega_i
+  double Lm[3][kMaxN];         // (2/h_d) l_i(-1) / omega_i
+  double Tp[kMaxN];            // l_a(+1): trace at the high face
+  double Tm[kMaxN];            // l_a(-1): trace at the low face
+  double xi[kMaxN];            // Gauss nodes on [-1, 1]
+  double wq[kMaxN];            // Gauss weights
+  double xe[kMaxN + 1];        // (N+1)-point Gauss nodes for error integrals
+  double we[kMaxN + 1];
+  double Le[(kMaxN + 1) * kMaxN];  // l_a(xe_p), entry [p*N + a]
+};
+
+struct MeshArgs {
+  int n[3];
+  int64_t ne;
+  int64_t es[3];  // element index stride per direction
+};
+
+enum UpdateMode { kModeRHS = 0, kMode2R = 1, kMode2N = 2 };
+
+struct VolArgs {
+  MeshArgs m;
+  const OpTables* tab;
+  double gamma;
+  int mode;        // UpdateMode
+  int stage, last; // stage index; last = 1 on the final stage of a step
+  double ca, cb;   // 2R: dt*a_m, dt*b_m ; 2N: A_m, B_m
+  double dt;
+  const double* in;  // stage input state (w, or r for 2R stages > 0)
+  double* w;         // solution (read + write)
+  double* x;         // 2R: r (write); 2N: q (read+write); RHS: k output
+  const void* fl;    // face fluxes [d][v][e][j] (storage type of the arithmetic)
+  void* tr;          // traces of the next stage input [d][side][v][e][j]
+  int write_traces;
+};
+
+struct FluxArgs {
+  MeshArgs m;
+  double gamma;
+  const void* tr;
+  void* fl;
+  // subdomain-face handling
+  int pe_mode;          // 0: all faces fresh; 1: apply ring rules on PE faces
+  int flux_kind;        // adg_flux
+  const int32_t* pe_slot;   // [d][e] -> PE face slot or -1
+  const int32_t* pe_iface;  // [slot] -> interface id
+  int64_t npe;              // PE faces
+  void* ring;               // [level][v][slot][j] (AT_TRACE: [level][2][v][slot][j])
+  int depth, head;          // ring depth, level written last (after this stage's store)
+  int store;                // write fresh value to ring[head] (stage 0 of a storing step)
+  int random;               // per-interface delays (random mode)
+  int uniform_delay;        // CAA: 0 on communication steps, k otherwise
+  int nterms;               // 1 (standard) or np+1 (AT)
+  uint64_t seed;
+  int64_t step;
+  int n_iface, dmax, np;
+  double ctab[kMaxCoefDelay][kMaxN];  // AT weights per delay for this stage
+};
+
+struct TraceArgs {
+  MeshArgs m;
+  const OpTables* tab;
+  const double* u;
+  void* tr;
+};
+
+// Launchers (one per arithmetic), implemented in the kernel translation units.
+// prec: 0 = FP64, 1 = FP32, 2 = FP32 pair.
+cudaError_t launch_trace(int prec, int dim, int N, const TraceArgs& a, cudaStream_t s);
+cudaError_t launch_flux(int prec, int dim, int N, const FluxArgs& a, cudaStream_t s);
+cudaError_t launch_vol(int prec, int dim, int N, const VolArgs& a, cudaStream_t s);
+bool kernels_available(int prec, int dim, int N);
+size_t storage_bytes(int prec);  // bytes per stored trace/flux value
+
+// Auxiliary kernels (FP64), in aux.cu.
+cudaError_t launch_init_vortex(int dim, int N, const MeshArgs& m, const double* lo,
+                               const double* h, const OpTables* tab, double gamma, double t,
+                               double beta, double x0, double y0, double Lx, double Ly,
+                               double* u, cudaStream_t s);
+cudaError_t launch_init_tgv(int N, const MeshArgs& m, const double* lo, const double* h,
+                            const OpTables* tab, double gamma, double mach, double* u,
+                            cudaStream_t s);
+cudaError_t launch_conservation(int dim, int N, const MeshArgs& m, const OpTables* tab,
+                                double J, const double* u, double* partial, double* out,
+                                int nblocks, cudaStream_t s);
+cudaError_t launch_max_speed(int dim, int N, const MeshArgs& m, double gamma, const double* u,
+                             double* partial, double* out, int nblocks, cudaStream_t s);
+cudaError_t launch_l2_vortex(int dim, int N, const MeshArgs& m, const double* lo,
+                             const double* h, const OpTables* tab, double gamma, double t,
+                             double beta, double x0, double y0, double Lx, double Ly,
+                             const double* u, double* partial, double* out, int nblocks,
+                             cudaStream_t s);
+cudaError_t launch_check_finite(int64_t n, const double* u, int* flag, cudaStream_t s);
+
+}  // namespace adg

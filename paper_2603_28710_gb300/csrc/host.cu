@@ -1,0 +1,880 @@
+// Host side of the ADG library: the C ABI of include/adg.h, the FP64 operator tables, the
+// delay schedules and the per-stage launch sequence.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/adg.h"
+#include "adg_internal.h"
+
+using namespace adg;
+
+struct adg_solver {
+  adg_mesh mesh{};
+  int dim = 2, degree = 1, N = 2, ND = 4, NF = 2, NV = 4;
+  int64_t ne = 0, ndof = 0;
+  int P[3] = {1, 1, 1};
+  int max_delay = 0;
+  adg_flux flux = ADG_FLUX_SYNC;
+  adg_options opt{};
+  int np = 1;
+  int stages = 0;
+  bool rk2n = false;
+  double rka[8] = {0}, rkb[8] = {0}, rkc[8] = {0};
+  double h[3] = {1, 1, 1};
+  double J = 1.0;
+  int prec = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  // device memory
+  double* w = nullptr;
+  double* x = nullptr;       // 2R: r ; 2N: q
+  void* tr = nullptr;        // traces
+  void* fl = nullptr;        // face fluxes
+  void* ring = nullptr;      // delayed-flux history
+  int32_t* pe_slot = nullptr;
+  int32_t* pe_iface = nullptr;
+  OpTables* tab_dev = nullptr;
+  double* red_partial = nullptr;
+  double* red_out = nullptr;
+  int* flag = nullptr;
+  double* tmp_u = nullptr;
+  double* tmp_k = nullptr;
+  int red_blocks = 0;
+  OpTables tab{};
+  MeshArgs margs{};
+  int64_t npe = 0;
+  int depth = 0, head = -1, n_iface = 0;
+  // run state
+  bool has_state = false, traces_valid = false;
+  int64_t step = 0;
+  double t = 0.0, dt = 0.0;
+  std::string err;
+  // kernel timing (adg_set_profiling)
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<int> ev_kind;  // kind of each recorded pair
+  size_t ev_used = 0;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+adg_status fail(adg_solver* s, adg_status st, const std::string& msg) {
+  if (s) s->err = msg;
+  else g_err = msg;
+  return st;
+}
+
+adg_status cuda_fail(adg_solver* s, cudaError_t e, const char* what) {
+  return fail(s, e == cudaErrorMemoryAllocation ? ADG_ERR_OOM : ADG_ERR_CUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define ADG_CUDA(S, call)                                    \
+  do {                                                       \
+    cudaError_t e__ = (call);                                \
+    if (e__ != cudaSuccess) return cuda_fail((S), e__, #call); \
+  } while (0)
+
+// ---- basis (Gauss-Legendre, Lagrange, barycentric derivative) -----------------------
+
+// Legendre P_n and P_n' by the three-term recurrence and P_k' = k P_{k-1} + x P_{k-1}'.
+void legendre_ld(int n, long double x, long double* p, long double* dp) {
+  long double pm1 = 1.0L, dpm1 = 0.0L, pk = x, dpk = 1.0L;
+  if (n == 0) { *p = 1.0L; *dp = 0.0L; return; }
+  for (int k = 2; k <= n; ++k) {
+    long double pn = ((2 * k - 1) * x * pk - (k - 1) * pm1) / k;
+    long double dpn = k * pk + x * dpk;
+    pm1 = pk; dpm1 = dpk;
+    pk = pn; dpk = dpn;
+  }
+  (void)dpm1;
+  *p = pk;
+  *dp = dpk;
+}
+
+void gauss_legendre(int n, double* xo, double* wo) {
+  const long double pi = 3.141592653589793238462643383279502884L;
+  long double xs[16], ws[16];
+  for (int i = 1; i <= n; ++i) {
+    // Tricomi's asymptotic first guess of the i-th largest root
+    long double th = pi * (4.0L * i - 1.0L) / (4.0L * n + 2.0L);
+    long double z = (1.0L - 1.0L / (8.0L * n * n) + 1.0L / (8.0L * n * n * n)) * cosl(th);
+    long double p, dp;
+    for (int it = 0; it < 60; ++it) {
+      legendre_ld(n, z, &p, &dp);
+      long double dz = p / dp;
+      z -= dz;
+      if (fabsl(dz) < 1e-19L) break;
+    }
+    legendre_ld(n, z, &p, &dp);
+    xs[n - i] = z;
+    ws[n - i] = 2.0L / ((1.0L - z * z) * dp * dp);
+  }
+  for (int i = 0; i < n; ++i) {
+    xo[i] = (double)xs[i];
+    wo[i] = (double)ws[i];
+  }
+}
+
+void bary_weights(int n, const long double* x, long double* lam) {
+  for (int j = 0; j < n; ++j) {
+    long double p = 1.0L;
+    for (int k = 0; k < n; ++k)
+      if (k != j) p *= (x[j] - x[k]);
+    lam[j] = 1.0L / p;
+  }
+}
+
+// l_j(y) for all j by the second barycentric formula
+void lagrange_at(int n, const long double* x, const long double* lam, long double y,
+                 long double* out) {
+  for (int j = 0; j < n; ++j)
+    if (y == x[j]) {
+      for (int k = 0; k < n; ++k) out[k] = (k == j) ? 1.0L : 0.0L;
+      return;
+    }
+  long double den = 0.0L;
+  for (int j = 0; j < n; ++j) den += lam[j] / (y - x[j]);
+  for (int j = 0; j < n; ++j) out[j] = (lam[j] / (y - x[j])) / den;
+}
+
+void build_tables(adg_solver* s) {
+  const int N = s->N;
+  OpTables& T = s->tab;
+  std::memset(&T, 0, sizeof(T));
+  double xd[16], wd[16];
+  gauss_legendre(N, xd, wd);
+  long double x[16], lam[16];
+  for (int i = 0; i < N; ++i) {
+    x[i] = xd[i];
+    T.xi[i] = xd[i];
+    T.wq[i] = wd[i];
+  }
+  bary_weights(N, x, lam);
+  // differentiation matrix Dm[a][i] = l_i'(x_a)
+  long double Dm[16][16];
+  for (int a = 0; a < N; ++a) {
+    long double diag = 0.0L;
+    for (int i = 0; i < N; ++i) {
+      if (i == a) continue;
+      Dm[a][i] = (lam[i] / lam[a]) / (x[a] - x[i]);
+      diag -= Dm[a][i];
+    }
+    Dm[a][a] = diag;
+  }
+  long double lp[16], lm[16];
+  lagrange_at(N, x, lam, 1.0L, lp);
+  lagrange_at(N, x, lam, -1.0L, lm);
+  for (int d = 0; d < 3; ++d) {
+    long double sc = 2.0L / (long double)s->h[d];
+    for (int i = 0; i < N; ++i) {
+      for (int a = 0; a < N; ++a)
+        T.Q[d][i * N + a] = (double)(sc * (long double)wd[a] * Dm[a][i] / (long double)wd[i]);
+      T.Lp[d][i] = (double)(sc * lp[i] / (long double)wd[i]);
+      T.Lm[d][i] = (double)(sc * lm[i] / (long double)wd[i]);
+    }
+  }
+  for (int a = 0; a < N; ++a) {
+    T.Tp[a] = (double)lp[a];
+    T.Tm[a] = (double)lm[a];
+  }
+  double xe[16], we[16];
+  gauss_legendre(N + 1, xe, we);
+  for (int p = 0; p < N + 1; ++p) {
+    T.xe[p] = xe[p];
+    T.we[p] = we[p];
+    long double l[16];
+    lagrange_at(N, x, lam, (long double)xe[p], l);
+    for (int a = 0; a < N; ++a) T.Le[p * N + a] = (double)l[a];
+  }
+}
+
+// ---- AT weights: Lagrange extrapolation to the stage time from levels -(km + l) ------
+void at_weights(int np, double km, double* c) {
+  for (int l = 0; l <= np; ++l) {
+    long double v = 1.0L;
+    for (int j = 0; j <= np; ++j)
+      if (j != l) v *= ((long double)km + j) / (long double)(j - l);
+    c[l] = (double)v;
+  }
+}
+
+// ---- Runge-Kutta coefficients ---------------------------------------------------------
+int rk_coeffs(adg_rk scheme, double* a, double* b, double* c) {
+  int s = 0;
+  bool two_n = false;
+  if (scheme == ADG_RK_2R_22) {
+    s = 2;
+    a[0] = 1.0; a[1] = 0.0;
+    b[0] = 0.5; b[1] = 0.5;
+  } else if (scheme == ADG_RK_2R_33) {
+    s = 3;
+    a[0] = 0.755726352; a[1] = 0.386954477; a[2] = 0.0;
+    b[0] = 0.245170287; b[1] = 0.184896052; b[2] = 0.569933661;
+  } else if (scheme == ADG_RK_2N_CK45) {
+    s = 5;
+    two_n = true;
+    const double A[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+                         -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
+    const double B[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+                         1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+                         2277821191437.0 / 14882151754819.0};
+    for (int i = 0; i < 5; ++i) { a[i] = A[i]; b[i] = B[i]; }
+  } else {
+    return 0;
+  }
+  // Stage abscissae: run the scheme on y' = 1 from y = 0 with dt = 1; the input of
+  // stage m then equals c_m.
+  long double y = 0.0L, q = 0.0L, r = 0.0L;
+  for (int m = 0; m < s; ++m) {
+    c[m] = (double)(two_n ? y : r);
+    if (two_n) {
+      q = (long double)a[m] * q + 1.0L;
+      y += (long double)b[m] * q;
+    } else {
+      long double y0 = y;
+      r = y0 + (long double)a[m];
+      y = y0 + (long double)b[m];
+    }
+  }
+  return s;
+}
+
+uint64_t splitmix64_host(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+int num_interfaces(int dim, const int* P) {
+  int nsub = 1, dirs = 0;
+  for (int d = 0; d < dim; ++d) {
+    nsub *= P[d];
+    if (P[d] > 1) ++dirs;
+  }
+  return nsub * dirs;
+}
+
+// Schedule of one step n: communication flag and delay counter in closed form.
+void caa_step(adg_flux flux, int L, int np, int64_t n, int* comm, int* k) {
+  if (flux == ADG_FLUX_SYNC) {
+    *comm = 1;
+    *k = 0;
+  } else if (flux == ADG_FLUX_STD_DELAYED) {
+    *k = (int)(n % L);
+    *comm = (*k == 0);
+  } else {
+    const int64_t cyc = (int64_t)L + np + 1;
+    const int ph = (int)(n % cyc);
+    *comm = ph < np + 1;
+    *k = *comm ? 0 : ph - np;
+  }
+}
+
+int random_delay(adg_flux flux, int np, uint64_t seed, int dmax, int64_t n, int nif, int f) {
+  if (flux == ADG_FLUX_SYNC) return 0;
+  int kt = (int)(splitmix64_host(seed ^ ((uint64_t)n * (uint64_t)nif + (uint64_t)f)) %
+                 (uint64_t)(dmax + 1));
+  int64_t need = (flux == ADG_FLUX_STD_DELAYED) ? kt : (int64_t)kt + np;
+  return (n - need < 0) ? 0 : kt;
+}
+
+adg_status schedule_impl(adg_flux flux, adg_delay_mode mode, int L, int np, int dim,
+                         const int* P, uint64_t seed, int dmax, int64_t n0, int n, int32_t* comm,
+                         int32_t* k, int32_t* iface_delay) {
+  const int nif = num_interfaces(dim, P);
+  for (int i = 0; i < n; ++i) {
+    const int64_t step = n0 + i;
+    if (mode == ADG_DELAY_RANDOM) {
+      int kmax = 0;
+      for (int f = 0; f < nif; ++f) {
+        int kt = random_delay(flux, np, seed, dmax, step, nif, f);
+        if (iface_delay) iface_delay[(int64_t)i * nif + f] = kt;
+        kmax = kt > kmax ? kt : kmax;
+      }
+      if (comm) comm[i] = kmax == 0;
+      if (k) k[i] = kmax;
+    } else {
+      int c, kk;
+      caa_step(flux, L, np, step, &c, &kk);
+      if (comm) comm[i] = c;
+      if (k) k[i] = kk;
+      if (iface_delay)
+        for (int f = 0; f < nif; ++f) iface_delay[(int64_t)i * nif + f] = kk;
+    }
+  }
+  return ADG_OK;
+}
+
+bool valid_degree(int dim, int degree) {
+  return degree >= 1 && (dim == 2 ? degree <= 7 : degree <= 5);
+}
+
+size_t prec_bytes(int prec) { return storage_bytes(prec); }
+
+// Event pair around one launch (profiling only).
+cudaError_t prof_begin(adg_solver* s, int kind) {
+  if (!s->profiling) return cudaSuccess;
+  if (s->ev_used + 2 > s->ev_pool.size()) {
+    for (int i = 0; i < 64; ++i) {
+      cudaEvent_t e;
+      cudaError_t err = cudaEventCreate(&e);
+      if (err != cudaSuccess) return err;
+      s->ev_pool.push_back(e);
+    }
+  }
+  if (s->ev_kind.size() < s->ev_pool.size() / 2) s->ev_kind.resize(s->ev_pool.size() / 2);
+  s->ev_kind[s->ev_used / 2] = kind;
+  return cudaEventRecord(s->ev_pool[s->ev_used], s->stream);
+}
+
+cudaError_t prof_end(adg_solver* s) {
+  if (!s->profiling) return cudaSuccess;
+  cudaError_t err = cudaEventRecord(s->ev_pool[s->ev_used + 1], s->stream);
+  s->ev_used += 2;
+  return err;
+}
+
+void free_all(adg_solver* s) {
+  for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
+  s->ev_pool.clear();
+  void* ptrs[] = {s->w, s->x, s->tr, s->fl, s->ring, s->pe_slot, s->pe_iface, s->tab_dev,
+                  s->red_partial, s->red_out, s->flag, s->tmp_u, s->tmp_k};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+}
+
+adg_status launch_traces_of(adg_solver* s, const double* u) {
+  TraceArgs ta{};
+  ta.m = s->margs;
+  ta.tab = s->tab_dev;
+  ta.u = u;
+  ta.tr = s->tr;
+  ADG_CUDA(s, launch_trace(s->prec, s->dim, s->N, ta, s->stream));
+  return ADG_OK;
+}
+
+FluxArgs base_flux_args(adg_solver* s) {
+  FluxArgs fa;
+  std::memset(&fa, 0, sizeof(fa));
+  fa.m = s->margs;
+  fa.gamma = s->opt.gamma;
+  fa.tr = s->tr;
+  fa.fl = s->fl;
+  fa.flux_kind = (int)s->flux;
+  fa.pe_slot = s->pe_slot;
+  fa.pe_iface = s->pe_iface;
+  fa.npe = s->npe;
+  fa.ring = s->ring;
+  fa.depth = s->depth;
+  fa.seed = s->opt.seed;
+  fa.n_iface = s->n_iface;
+  fa.dmax = s->opt.random_delay_max;
+  fa.np = s->np;
+  fa.nterms = (s->flux == ADG_FLUX_STD_DELAYED) ? 1 : s->np + 1;
+  return fa;
+}
+
+adg_status after_state_set(adg_solver* s) {
+  s->has_state = true;
+  s->step = 0;
+  s->t = 0.0;
+  s->head = -1;
+  if (s->opt.dt > 0) {
+    s->dt = s->opt.dt;
+  } else {
+    ADG_CUDA(s, launch_max_speed(s->dim, s->N, s->margs, s->opt.gamma, s->w, s->red_partial,
+                                 s->red_out, s->red_blocks, s->stream));
+    double smax = 0;
+    ADG_CUDA(s, cudaMemcpyAsync(&smax, s->red_out, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    ADG_CUDA(s, cudaStreamSynchronize(s->stream));
+    if (!(smax > 0) || !std::isfinite(smax))
+      return fail(s, ADG_ERR_NONFINITE, "state has no finite positive signal speed");
+    double hmin = s->h[0];
+    for (int d = 1; d < s->dim; ++d) hmin = s->h[d] < hmin ? s->h[d] : hmin;
+    double dt = s->opt.cfl * hmin / ((2.0 * s->degree + 1.0) * smax);
+    if (s->opt.t_end > 0) dt = s->opt.t_end / std::ceil(s->opt.t_end / dt);
+    s->dt = dt;
+  }
+  adg_status st = launch_traces_of(s, s->w);
+  if (st != ADG_OK) return st;
+  s->traces_valid = true;
+  return ADG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+adg_status adg_default_options(adg_options* opt) {
+  if (!opt) return fail(nullptr, ADG_ERR_INVALID, "opt is NULL");
+  std::memset(opt, 0, sizeof(*opt));
+  opt->rk = ADG_RK_2N_CK45;
+  opt->dt = 0.0;
+  opt->cfl = 0.1;
+  opt->t_end = 0.0;
+  opt->gamma = 1.4;
+  opt->delay_mode = ADG_DELAY_CAA;
+  opt->seed = 0;
+  opt->random_delay_max = 0;
+  opt->at_np = 0;
+  opt->precision = ADG_PREC_FP64;
+  opt->cuda_stream = nullptr;
+  return ADG_OK;
+}
+
+adg_status adg_create(const adg_mesh* mesh, int degree, const int P[3], int max_delay,
+                      adg_flux flux, const adg_options* opt, adg_solver** out) {
+  if (!out) return fail(nullptr, ADG_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!mesh || !P) return fail(nullptr, ADG_ERR_INVALID, "mesh or P is NULL");
+  if (mesh->dim != 2 && mesh->dim != 3) return fail(nullptr, ADG_ERR_INVALID, "dim must be 2 or 3");
+  if (degree < 1 || degree > 7) return fail(nullptr, ADG_ERR_INVALID, "degree must be in 1..7");
+  if (!valid_degree(mesh->dim, degree))
+    return fail(nullptr, ADG_ERR_UNSUPPORTED, "3D is built for degree 1..5");
+  if ((int)flux < 0 || (int)flux > 3) return fail(nullptr, ADG_ERR_INVALID, "unknown flux");
+  adg_options o;
+  if (opt) o = *opt;
+  else adg_default_options(&o);
+  if ((int)o.rk < 0 || (int)o.rk > 2) return fail(nullptr, ADG_ERR_INVALID, "unknown rk scheme");
+  if ((int)o.precision < 0 || (int)o.precision > 2)
+    return fail(nullptr, ADG_ERR_INVALID, "unknown precision");
+  if (!(o.gamma > 1.0)) return fail(nullptr, ADG_ERR_INVALID, "gamma must exceed 1");
+  if (o.dt <= 0 && !(o.cfl > 0)) return fail(nullptr, ADG_ERR_INVALID, "need dt > 0 or cfl > 0");
+  if (o.delay_mode != ADG_DELAY_CAA && o.delay_mode != ADG_DELAY_RANDOM)
+    return fail(nullptr, ADG_ERR_INVALID, "unknown delay mode");
+  if (o.delay_mode == ADG_DELAY_RANDOM && (o.random_delay_max < 0 || o.random_delay_max > 15))
+    return fail(nullptr, ADG_ERR_INVALID, "random_delay_max must be in 0..15");
+  const int np = o.at_np > 0 ? o.at_np : degree;
+  if (np > 7) return fail(nullptr, ADG_ERR_INVALID, "at_np must be <= 7");
+  if (flux != ADG_FLUX_SYNC && o.delay_mode == ADG_DELAY_CAA) {
+    int lmin = (flux == ADG_FLUX_STD_DELAYED) ? 1 : 0;
+    if (max_delay < lmin || max_delay > 15)
+      return fail(nullptr, ADG_ERR_INVALID, "max_delay out of range (1..15 standard, 0..15 AT)");
+  }
+  int64_t ne = 1;
+  for (int d = 0; d < mesh->dim; ++d) {
+    if (mesh->n_elem[d] < 1) return fail(nullptr, ADG_ERR_INVALID, "n_elem must be >= 1");
+    if (P[d] < 1 || mesh->n_elem[d] % P[d] != 0)
+      return fail(nullptr, ADG_ERR_INVALID, "P[d] must divide n_elem[d]");
+    if (!(mesh->hi[d] > mesh->lo[d])) return fail(nullptr, ADG_ERR_INVALID, "hi must exceed lo");
+    ne *= mesh->n_elem[d];
+  }
+  if (!kernels_available((int)o.precision, mesh->dim, degree + 1))
+    return fail(nullptr, ADG_ERR_UNSUPPORTED, "no kernels built for this precision/degree");
+
+  adg_solver* s = new (std::nothrow) adg_solver();
+  if (!s) return fail(nullptr, ADG_ERR_OOM, "host allocation failed");
+  s->mesh = *mesh;
+  s->dim = mesh->dim;
+  s->degree = degree;
+  s->N = degree + 1;
+  s->NV = s->dim + 2;
+  s->ND = s->dim == 3 ? s->N * s->N * s->N : s->N * s->N;
+  s->NF = s->ND / s->N;
+  s->ne = ne;
+  s->ndof = (int64_t)s->NV * ne * s->ND;
+  for (int d = 0; d < 3; ++d) s->P[d] = d < s->dim ? P[d] : 1;
+  s->max_delay = max_delay;
+  s->flux = flux;
+  s->opt = o;
+  s->np = np;
+  s->prec = (int)o.precision;
+  s->stages = rk_coeffs(o.rk, s->rka, s->rkb, s->rkc);
+  s->rk2n = (o.rk == ADG_RK_2N_CK45);
+  s->J = 1.0;
+  for (int d = 0; d < 3; ++d) {
+    s->h[d] = d < s->dim ? (mesh->hi[d] - mesh->lo[d]) / mesh->n_elem[d] : 1.0;
+    if (d < s->dim) s->J *= s->h[d] / 2.0;
+  }
+  s->margs.n[0] = mesh->n_elem[0];
+  s->margs.n[1] = mesh->n_elem[1];
+  s->margs.n[2] = s->dim == 3 ? mesh->n_elem[2] : 1;
+  s->margs.ne = ne;
+  s->margs.es[0] = 1;
+  s->margs.es[1] = s->margs.n[0];
+  s->margs.es[2] = (int64_t)s->margs.n[0] * s->margs.n[1];
+  build_tables(s);
+
+  // subdomain faces: face (d, e) joins e and its +d neighbour; it lies between two
+  // subdomains iff P[d] > 1 and e is the last element of its block along d.
+  s->n_iface = num_interfaces(s->dim, s->P);
+  int32_t* slot_h = nullptr;
+  int32_t* iface_h = nullptr;
+  if (flux != ADG_FLUX_SYNC) {
+    slot_h = new (std::nothrow) int32_t[(size_t)s->dim * ne];
+    iface_h = new (std::nothrow) int32_t[(size_t)s->dim * ne + 1];
+    if (!slot_h || !iface_h) {
+      delete[] slot_h;
+      delete[] iface_h;
+      delete s;
+      return fail(nullptr, ADG_ERR_OOM, "host allocation failed");
+    }
+    int nsub = s->P[0] * s->P[1] * s->P[2];
+    int off = 0;
+    for (int d = 0; d < s->dim; ++d) {
+      const int bs = s->margs.n[d] / s->P[d];
+      for (int64_t e = 0; e < ne; ++e) {
+        int c[3] = {(int)(e % s->margs.n[0]), (int)((e / s->margs.n[0]) % s->margs.n[1]),
+                    (int)(e / ((int64_t)s->margs.n[0] * s->margs.n[1]))};
+        bool pe = s->P[d] > 1 && (c[d] + 1) % bs == 0;
+        if (pe) {
+          int sub = 0;
+          for (int dd = s->dim - 1; dd >= 0; --dd)
+            sub = sub * s->P[dd] + c[dd] / (s->margs.n[dd] / s->P[dd]);
+          iface_h[s->npe] = off + sub;
+          slot_h[(int64_t)d * ne + e] = (int32_t)s->npe++;
+        } else {
+          slot_h[(int64_t)d * ne + e] = -1;
+        }
+      }
+      if (s->P[d] > 1) off += nsub;
+    }
+    if (o.delay_mode == ADG_DELAY_RANDOM)
+      s->depth = o.random_delay_max + (flux == ADG_FLUX_STD_DELAYED ? 0 : np) + 1;
+    else
+      s->depth = (flux == ADG_FLUX_STD_DELAYED) ? 1 : np + 1;
+  }
+
+  cudaError_t ce = cudaSuccess;
+  auto alloc = [&](void** p, size_t bytes) {
+    if (ce == cudaSuccess && bytes > 0) ce = cudaMalloc(p, bytes);
+  };
+  const size_t sb = prec_bytes(s->prec);
+  const size_t nst = (size_t)s->ndof;
+  const size_t ntr = (size_t)2 * s->dim * s->NV * ne * s->NF;
+  const size_t nfl = (size_t)s->dim * s->NV * ne * s->NF;
+  s->red_blocks = 152 * 4;
+  alloc((void**)&s->w, nst * sizeof(double));
+  alloc((void**)&s->x, nst * sizeof(double));
+  alloc(&s->tr, ntr * sb);
+  alloc(&s->fl, nfl * sb);
+  alloc((void**)&s->tab_dev, sizeof(OpTables));
+  alloc((void**)&s->red_partial, (size_t)s->red_blocks * 5 * sizeof(double));
+  alloc((void**)&s->red_out, 8 * sizeof(double));
+  alloc((void**)&s->flag, sizeof(int));
+  if (flux != ADG_FLUX_SYNC) {
+    alloc((void**)&s->pe_slot, (size_t)s->dim * ne * sizeof(int32_t));
+    alloc((void**)&s->pe_iface, (size_t)(s->npe + 1) * sizeof(int32_t));
+    size_t ringn = (size_t)s->depth * (flux == ADG_FLUX_AT_TRACE ? 2 : 1) * s->NV * s->npe * s->NF;
+    alloc(&s->ring, (ringn + 1) * sb);
+  }
+  if (ce == cudaSuccess) {
+    if (o.cuda_stream) {
+      s->stream = (cudaStream_t)o.cuda_stream;
+    } else {
+      ce = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+      s->own_stream = (ce == cudaSuccess);
+    }
+  }
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync(s->tab_dev, &s->tab, sizeof(OpTables), cudaMemcpyHostToDevice, s->stream);
+  if (ce == cudaSuccess && flux != ADG_FLUX_SYNC) {
+    ce = cudaMemcpyAsync(s->pe_slot, slot_h, (size_t)s->dim * ne * sizeof(int32_t),
+                         cudaMemcpyHostToDevice, s->stream);
+    if (ce == cudaSuccess && s->npe > 0)
+      ce = cudaMemcpyAsync(s->pe_iface, iface_h, (size_t)s->npe * sizeof(int32_t),
+                           cudaMemcpyHostToDevice, s->stream);
+  }
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s->stream);
+  delete[] slot_h;
+  delete[] iface_h;
+  if (ce != cudaSuccess) {
+    adg_status st = cuda_fail(nullptr, ce, "adg_create");
+    free_all(s);
+    delete s;
+    return st;
+  }
+  *out = s;
+  return ADG_OK;
+}
+
+adg_status adg_set_state(adg_solver* s, const double* u, int64_t count, int on_device) {
+  if (!s) return fail(nullptr, ADG_ERR_INVALID, "handle is NULL");
+  if (!u) return fail(s, ADG_ERR_INVALID, "u is NULL");
+  if (count != s->ndof) return fail(s, ADG_ERR_INVALID, "count does not match n_dof");
+  ADG_CUDA(s, cudaMemcpyAsync(s->w, u, count * sizeof(double),
+                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                              s->stream));
+  return after_state_set(s);
+}
+
+adg_status adg_init_vortex(adg_solver* s, double t, double beta, double x0, double y0) {
+  if (!s) return fail(nullptr, ADG_ERR_INVALID, "handle is NULL");
+  const double Lx = s->mesh.hi[0] - s->mesh.lo[0], Ly = s->mesh.hi[1] - s->mesh.lo[1];
+  ADG_CUDA(s, launch_init_vortex(s->dim, s->N, s->margs, s->mesh.lo, s->h, s->tab_dev,
+                                 s->opt.gamma, t, beta, x0, y0, Lx, Ly, s->w, s->stream));
+  return after_state_set(s);
+}
+
+adg_status adg_init_tgv(adg_solver* s, double mach) {
+  if (!s) return fail(nullptr, ADG_ERR_INVALID, "handle is NULL");
+  if (s->dim != 3) return fail(s, ADG_ERR_INVALID, "the Taylor-Green vortex is 3D");
+  if (!(mach > 0)) return fail(s, ADG_ERR_INVALID, "mach must be positive");
+  ADG_CUDA(s, launch_init_tgv(s->N, s->margs, s->mesh.lo, s->h, s->tab_dev, s->opt.gamma, mach,
+                              s->w, s->stream));
+  return after_state_set(s);
+}
+
+adg_status adg_step(adg_solver* s, int n_steps) {
+  if (!s) return fail(nullptr, ADG_ERR_INVALID, "handle is NULL");
+  if (n_steps < 0) return fail(s, ADG_ERR_INVALID, "n_steps must be >= 0");
+  if (!s->has_state) return fail(s, ADG_ERR_STATE, "no state: call adg_set_state first");
+  if (!s->traces_valid) {
+    adg_status st = launch_traces_of(s, s->w);
+    if (st != ADG_OK) return st;
+    s->traces_valid = true;
+  }
+  const bool pe = s->flux != ADG_FLUX_SYNC && s->npe > 0;
+  const bool random = s->opt.delay_mode == ADG_DELAY_RANDOM;
+  for (int it = 0; it < n_steps; ++it) {
+    const int64_t n = s->step;
+    int comm = 1, k = 0;
+    if (!random) caa_step(s->flux, s->max_delay, s->np, n, &comm, &k);
+    const bool store_step = pe && (random || comm);
+    for (int m = 0; m < s->stages; ++m) {
+      FluxArgs fa = base_flux_args(s);
+      fa.pe_mode = pe ? 1 : 0;
+      if (pe) {
+        if (store_step && m == 0) {
+          s->head = (s->head + 1) % s->depth;
+          fa.store = 1;
+        }
+        fa.head = s->head < 0 ? 0 : s->head;
+        fa.random = random ? 1 : 0;
+        fa.uniform_delay = random ? 0 : (comm ? 0 : k);
+        fa.step = n;
+        const int kmax = random ? s->opt.random_delay_max : (comm ? 0 : k);
+        for (int kt = 0; kt <= kmax && kt < kMaxCoefDelay; ++kt) {
+          if (s->flux == ADG_FLUX_STD_DELAYED) {
+            fa.ctab[kt][0] = 1.0;
+          } else {
+            at_weights(s->np, kt + s->rkc[m], fa.ctab[kt]);
+          }
+        }
+      }
+      ADG_CUDA(s, prof_begin(s, 0));
+      ADG_CUDA(s, launch_flux(s->prec, s->dim, s->N, fa, s->stream));
+      ADG_CUDA(s, prof_end(s));
+      VolArgs va;
+      std::memset(&va, 0, sizeof(va));
+      va.m = s->margs;
+      va.tab = s->tab_dev;
+      va.gamma = s->opt.gamma;
+      va.mode = s->rk2n ? kMode2N : kMode2R;
+      va.stage = m;
+      va.last = (m == s->stages - 1);
+      va.dt = s->dt;
+      if (s->rk2n) {
+        va.ca = s->rka[m];
+        va.cb = s->rkb[m];
+        va.in = s->w;
+      } else {
+        va.ca = s->dt * s->rka[m];
+        va.cb = s->dt * s->rkb[m];
+        va.in = (m == 0) ? s->w : s->x;
+      }
+      va.w = s->w;
+      va.x = s->x;
+      va.fl = s->fl;
+      va.tr = s->tr;
+      va.write_traces = 1;
+      ADG_CUDA(s, prof_begin(s, 1));
+      ADG_CUDA(s, launch_vol(s->prec, s->dim, s->N, va, s->stream));
+      ADG_CUDA(s, prof_end(s));
+    }
+    s->step += 1;
+    s->t += s->dt;
+  }
+  return ADG_OK;
+}
+
+adg_status adg_get_state(adg_solver* s, double* u, int64_t count, int on_device) {
+  if (!s) return fail(nullptr, ADG_ERR_INVALID, "handle is NULL");
+  if (!u) return fail(s, ADG_ERR_INVALID, "u is NULL");
+  if (count != s->ndof) return fail(s, ADG_ERR_INVALID, "count does not match n_dof");
+  ADG_CUDA(s, cudaMemcpyAsync(u, s->w, count * sizeof(double),
+                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                              s->stream));
+  ADG_CUDA(s, cudaStreamSynchronize(s->stream));
+  return ADG_OK;
+}
+
+adg_status adg_rhs(adg_solver* s, const double* u, double* k, int64_t count, int on_device) {
+  if (!s) return fail(nullptr, ADG_ERR_INVALID, "handle is NULL");
+  if (!u || !k) return fail(s, ADG_ERR_INVALID, "u or k is NULL");
+  if (count != s->ndof) return fail(s, ADG_ERR_INVALID, "count does not match n_dof");
+  const size_t bytes = (size_t)count * sizeof(double);
+  if (!on_device) {
+    if (!s->tmp_u) ADG_CUDA(s, cudaMalloc((void**)&s->tmp_u, bytes));
+    if (!s->tmp_k) ADG_CUDA(s, cudaMalloc((void**)&s->tmp_k, bytes));
+    ADG_CUDA(s, cudaMemcpyAsync(s->tmp_u, u, bytes, cudaMemcpyHostToDevice, s->stream));
+  }
+  const double* ud = on_device ? u : s->tmp_u;
+  double* kd = on_device ? k : s->tmp_k;
+  adg_status st = launch_traces_of(s, ud);
+  if (st != ADG_OK) return st;
+  s->traces_valid = false;
+  FluxArgs fa = base_flux_args(s);
+  fa.pe_mode = 0;
+  ADG_CUDA(s, launch_flux(s->prec, s->dim, s->N, fa, s->stream));
+  VolArgs va;
+  std::memset(&va, 0, sizeof(va));
+  va.m = s->margs;
+  va.tab = s->tab_dev;
+  va.gamma = s->opt.gamma;
+  va.mode = kModeRHS;
+  va.in = ud;
+  va.x = kd;
+  va.fl = s->fl;
+  va.tr = s->tr;
+  va.write_traces = 0;
+  ADG_CUDA(s, launch_vol(s->prec, s->dim, s->N, va, s->stream));
+  if (!on_device)
+    ADG_CUDA(s, cudaMemcpyAsync(k, s->tmp_k, bytes, cudaMemcpyDeviceToHost, s->stream));
+  ADG_CUDA(s, cudaStreamSynchronize(s->stream));
+  return ADG_OK;
+}
+
+adg_status adg_get_schedule(const adg_solver* s, int64_t n0, int n, int32_t* comm, int32_t* k,
+                            int32_t* iface_delay) {
+  if (!s) return fail(nullptr, ADG_ERR_INVALID, "handle is NULL");
+  if (n < 0 || n0 < 0 || !comm || !k)
+    return fail(const_cast<adg_solver*>(s), ADG_ERR_INVALID, "bad schedule arguments");
+  return schedule_impl(s->flux, s->opt.delay_mode, s->max_delay, s->np, s->dim, s->P,
+                       s->opt.seed, s->opt.random_delay_max, n0, n, comm, k, iface_delay);
+}
+
+adg_status adg_info(const adg_solver* s, double* t, int64_t* step, double* dt, int64_t* n_dof) {
+  if (!s) return fail(nullptr, ADG_ERR_INVALID, "handle is NULL");
+  if (t) *t = s->t;
+  if (step) *step = s->step;
+  if (dt) *dt = s->dt;
+  if (n_dof) *n_dof = s->ndof;
+  return ADG_OK;
+}
+
+adg_status adg_conservation(adg_solver* s, double* sums) {
+  if (!s) return fail(nullptr, ADG_ERR_INVALID, "handle is NULL");
+  if (!sums) return fail(s, ADG_ERR_INVALID, "sums is NULL");
+  ADG_CUDA(s, launch_conservation(s->dim, s->N, s->margs, s->tab_dev, s->J, s->w, s->red_partial,
+                                  s->red_out, s->red_blocks, s->stream));
+  ADG_CUDA(s, cudaMemcpyAsync(sums, s->red_out, s->NV * sizeof(double), cudaMemcpyDeviceToHost,
+                              s->stream));
+  ADG_CUDA(s, cudaStreamSynchronize(s->stream));
+  return ADG_OK;
+}
+
+adg_status adg_l2_error_vortex(adg_solver* s, double t, double beta, double x0, double y0,
+                               double* err3) {
+  if (!s) return fail(nullptr, ADG_ERR_INVALID, "handle is NULL");
+  if (!err3) return fail(s, ADG_ERR_INVALID, "err3 is NULL");
+  const double Lx = s->mesh.hi[0] - s->mesh.lo[0], Ly = s->mesh.hi[1] - s->mesh.lo[1];
+  ADG_CUDA(s, launch_l2_vortex(s->dim, s->N, s->margs, s->mesh.lo, s->h, s->tab_dev, s->opt.gamma,
+                               t, beta, x0, y0, Lx, Ly, s->w, s->red_partial, s->red_out,
+                               s->red_blocks, s->stream));
+  double sq[3];
+  ADG_CUDA(s, cudaMemcpyAsync(sq, s->red_out, 3 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  ADG_CUDA(s, cudaStreamSynchronize(s->stream));
+  for (int i = 0; i < 3; ++i) err3[i] = std::sqrt(sq[i]);
+  return ADG_OK;
+}
+
+adg_status adg_check_finite(adg_solver* s) {
+  if (!s) return fail(nullptr, ADG_ERR_INVALID, "handle is NULL");
+  ADG_CUDA(s, launch_check_finite(s->ndof, s->w, s->flag, s->stream));
+  int f = 0;
+  ADG_CUDA(s, cudaMemcpyAsync(&f, s->flag, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+  ADG_CUDA(s, cudaStreamSynchronize(s->stream));
+  if (f) return fail(s, ADG_ERR_NONFINITE, "state holds NaN or Inf");
+  return ADG_OK;
+}
+
+adg_status adg_set_profiling(adg_solver* s, int enable) {
+  if (!s) return fail(nullptr, ADG_ERR_INVALID, "handle is NULL");
+  s->profiling = enable != 0;
+  s->ev_used = 0;
+  return ADG_OK;
+}
+
+adg_status adg_get_profile(adg_solver* s, double* ms, int64_t* launches) {
+  if (!s) return fail(nullptr, ADG_ERR_INVALID, "handle is NULL");
+  if (!ms || !launches) return fail(s, ADG_ERR_INVALID, "ms or launches is NULL");
+  ms[0] = ms[1] = 0.0;
+  launches[0] = launches[1] = 0;
+  ADG_CUDA(s, cudaStreamSynchronize(s->stream));
+  for (size_t i = 0; i + 1 < s->ev_used; i += 2) {
+    float t = 0.f;
+    ADG_CUDA(s, cudaEventElapsedTime(&t, s->ev_pool[i], s->ev_pool[i + 1]));
+    int kind = s->ev_kind[i / 2];
+    ms[kind] += t;
+    launches[kind] += 1;
+  }
+  s->ev_used = 0;
+  return ADG_OK;
+}
+
+const char* adg_last_error(const adg_solver* s) { return s ? s->err.c_str() : g_err.c_str(); }
+
+void adg_destroy(adg_solver* s) {
+  if (!s) return;
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  free_all(s);
+  delete s;
+}
+
+adg_status adg_host_gauss(int n, double* x, double* w) {
+  if (n < 1 || n > 9 || !x || !w) return fail(nullptr, ADG_ERR_INVALID, "bad arguments");
+  gauss_legendre(n, x, w);
+  return ADG_OK;
+}
+
+adg_status adg_host_at_coeffs(int np, double km, double* c) {
+  if (np < 0 || np > 7 || !c) return fail(nullptr, ADG_ERR_INVALID, "bad arguments");
+  at_weights(np, km, c);
+  return ADG_OK;
+}
+
+adg_status adg_host_rk(adg_rk scheme, int* stages, double* a, double* b, double* c) {
+  if (!stages || !a || !b || !c) return fail(nullptr, ADG_ERR_INVALID, "bad arguments");
+  double ta[8], tb[8], tc[8];
+  int s = rk_coeffs(scheme, ta, tb, tc);
+  if (!s) return fail(nullptr, ADG_ERR_INVALID, "unknown scheme");
+  *stages = s;
+  for (int i = 0; i < s; ++i) {
+    a[i] = ta[i];
+    b[i] = tb[i];
+    c[i] = tc[i];
+  }
+  return ADG_OK;
+}
+
+adg_status adg_host_schedule(adg_flux flux, adg_delay_mode mode, int max_delay, int np, int dim,
+                             const int P[3], uint64_t seed, int random_delay_max, int64_t n0,
+                             int n, int32_t* comm, int32_t* k, int32_t* iface_delay) {
+  if (!P || !comm || !k || n < 0 || n0 < 0 || (dim != 2 && dim != 3))
+    return fail(nullptr, ADG_ERR_INVALID, "bad arguments");
+  if (mode == ADG_DELAY_CAA && flux == ADG_FLUX_STD_DELAYED && max_delay < 1)
+    return fail(nullptr, ADG_ERR_INVALID, "max_delay must be >= 1");
+  int Pd[3] = {P[0], P[1], dim == 3 ? P[2] : 1};
+  return schedule_impl(flux, mode, max_delay, np, dim, Pd, seed, random_delay_max, n0, n, comm, k,
+                       iface_delay);
+}
+
+int adg_host_num_interfaces(int dim, const int P[3]) {
+  if (!P || (dim != 2 && dim != 3)) return -1;
+  int Pd[3] = {P[0], P[1], dim == 3 ? P[2] : 1};
+  return num_interfaces(dim, Pd);
+}
+
+}  // extern "C"

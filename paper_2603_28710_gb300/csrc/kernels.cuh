@@ -1,0 +1,479 @@
+// Kernel templates of the ADG right-hand side, parameterised by dimension D, nodes per
+// direction N = degree + 1 and the arithmetic type R of the operator (double, float or
+// the FP32-pair type of df64.cuh).  The solution and the Runge-Kutta registers are FP64
+// in every variant.
+//
+// Per Runge-Kutta stage the solver runs two kernels:
+//   flux_kernel : one thread per (direction, face, face node): numerical flux of Eq. 8-9
+//                 from the two stored traces; on faces between subdomains it applies the
+//                 delayed / AT rules of Algorithms 2-3 (Eq. 13-14) against a ring buffer.
+//   vol_kernel  : one thread per node, a tile of elements per block: pointwise Euler flux
+//                 (Eq. 2), sum-factorised weak derivative along each direction, face lift,
+//                 inverse mass (diagonal for collocated Gauss points; folded into the
+//                 tables), the low-storage RK update (Eq. 10 or the 2N form), and the
+//                 face traces of the next stage input.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "adg_internal.h"
+#include "arith.cuh"
+
+namespace adg {
+
+template <int B, int E>
+struct IPow { static constexpr int value = B * IPow<B, E - 1>::value; };
+template <int B>
+struct IPow<B, 0> { static constexpr int value = 1; };
+
+// Elements per block: about 128 threads per block, one thread per node.
+template <int D, int N>
+struct Tile {
+  static constexpr int ND = IPow<N, D>::value;
+  static constexpr int NF = ND / N;
+  static constexpr int NV = D + 2;
+  static constexpr int EPB = (128 / ND) > 0 ? (128 / ND) : 1;
+  static constexpr int THREADS = EPB * ND;
+};
+
+__device__ __forceinline__ void elem_coords(const MeshArgs& m, int64_t e, int* c) {
+  int64_t t = e;
+  c[0] = (int)(t % m.n[0]);
+  t /= m.n[0];
+  c[1] = (int)(t % m.n[1]);
+  t /= m.n[1];
+  c[2] = (int)t;
+}
+
+// index of the neighbour of element e (coordinates c) one step s (+1/-1) along d, periodic
+__device__ __forceinline__ int64_t elem_shift(const MeshArgs& m, int64_t e, const int* c, int d,
+                                              int s) {
+  int k = c[d] + s;
+  if (k < 0) k += m.n[d];
+  if (k >= m.n[d]) k -= m.n[d];
+  return e + (int64_t)(k - c[d]) * m.es[d];
+}
+
+// Pointwise Euler flux columns F_d(w), d < D (Eq. 2-3, no source).
+template <int D, typename R>
+__device__ __forceinline__ void euler_flux_all(const R* w, R gm1, R (*F)[D + 2]) {
+  R irho = r_rcp(w[0]);
+  R u[D];
+  R kin2 = R(0.0);
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    u[d] = w[1 + d] * irho;
+    kin2 = r_fma(w[1 + d], u[d], kin2);
+  }
+  R p = gm1 * (w[D + 1] - R(0.5) * kin2);
+  R ep = w[D + 1] + p;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    F[d][0] = w[1 + d];
+#pragma unroll
+    for (int c = 0; c < D; ++c) F[d][1 + c] = w[1 + c] * u[d];
+    F[d][1 + d] = F[d][1 + d] + p;
+    F[d][D + 1] = ep * u[d];
+  }
+}
+
+// Rusanov flux along +e_d (Eq. 8) with lambda = 1/2 max(sqrt(|u|^2 + c^2)) (Eq. 9).
+template <int D, typename R>
+__device__ __forceinline__ void llf_flux(const R* wm, const R* wp, int d, R gamma, R* f) {
+  constexpr int NV = D + 2;
+  R gm1 = gamma - R(1.0);
+  R s2[2];
+  R fd[2][NV];
+  const R* ws[2] = {wm, wp};
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    const R* w = ws[side];
+    R irho = r_rcp(w[0]);
+    R u2 = R(0.0), kin2 = R(0.0), ud = R(0.0);
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      R uc = w[1 + c] * irho;
+      u2 = r_fma(uc, uc, u2);
+      kin2 = r_fma(w[1 + c], uc, kin2);
+      if (c == d) ud = uc;
+    }
+    R p = gm1 * (w[D + 1] - R(0.5) * kin2);
+    s2[side] = u2 + gamma * p * irho;
+    fd[side][0] = w[1 + d];
+#pragma unroll
+    for (int c = 0; c < D; ++c) fd[side][1 + c] = w[1 + c] * ud;
+    fd[side][1 + d] = fd[side][1 + d] + p;
+    fd[side][D + 1] = (w[D + 1] + p) * ud;
+  }
+  R lam = R(0.5) * r_sqrt(r_max(s2[0], s2[1]));
+  R hl = R(0.5) * lam;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) f[v] = R(0.5) * (fd[0][v] + fd[1][v]) + hl * (wm[v] - wp[v]);
+}
+
+// Transverse coordinates of face node j of a face normal to d -> base node index of the
+// line of nodes along d through it.
+template <int D, int N>
+__device__ __forceinline__ int line_base(int d, int j) {
+  int base = 0, stride = 1, t = j;
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    if (c != d) {
+      base += (t % N) * stride;
+      t /= N;
+    }
+    stride *= N;
+  }
+  return base;
+}
+
+// Face node index of volume node (ix) on a face normal to d.
+template <int D, int N>
+__device__ __forceinline__ int face_index(int d, const int* ix) {
+  int j = 0, stride = 1;
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    if (c != d) {
+      j += ix[c] * stride;
+      stride *= N;
+    }
+  }
+  return j;
+}
+
+// Traces of a tile of elements held in shared memory sX[el][v][node] -> tr.
+template <int D, int N, typename R>
+__device__ __forceinline__ void write_traces(const MeshArgs& m, const OpTables* tab, const R* sX,
+                                             int64_t e0, typename Arith<R>::S* tr) {
+  using T = Tile<D, N>;
+  constexpr int ND = T::ND, NF = T::NF, NV = T::NV, EPB = T::EPB;
+  constexpr int TOTAL = EPB * 2 * D * NV * NF;
+  for (int g = threadIdx.x; g < TOTAL; g += blockDim.x) {
+    int jj = g % (EPB * NF);
+    int rest = g / (EPB * NF);  // (d*2 + side)*NV + v
+    int el = jj / NF, j = jj - el * NF;
+    int64_t e = e0 + el;
+    if (e >= m.ne) continue;
+    int v = rest % NV, ds = rest / NV;
+    int d = ds >> 1, side = ds & 1;
+    int base = line_base<D, N>(d, j);
+    int stride = 1;
+    for (int c = 0; c < d; ++c) stride *= N;
+    const double* tw = side ? tab->Tp : tab->Tm;
+    R acc = R(0.0);
+#pragma unroll
+    for (int a = 0; a < N; ++a) acc = r_fma(R(tw[a]), sX[(el * NV + v) * ND + base + a * stride], acc);
+    Arith<R>::store(tr + ((int64_t)(ds * NV + v) * m.ne + e) * NF + j, acc);
+  }
+}
+
+template <int D, int N, typename R>
+__global__ void __launch_bounds__(Tile<D, N>::THREADS) trace_kernel(const TraceArgs A) {
+  using T = Tile<D, N>;
+  constexpr int ND = T::ND, NV = T::NV, EPB = T::EPB;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* sX = reinterpret_cast<R*>(smem_raw);
+  const int el = threadIdx.x / ND, node = threadIdx.x - el * ND;
+  const int64_t e0 = (int64_t)blockIdx.x * EPB;
+  const int64_t e = e0 + el;
+  if (e < A.m.ne) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) sX[(el * NV + v) * ND + node] = R(A.u[((int64_t)v * A.m.ne + e) * ND + node]);
+  }
+  __syncthreads();
+  write_traces<D, N, R>(A.m, A.tab, sX, e0, reinterpret_cast<typename Arith<R>::S*>(A.tr));
+}
+
+template <int D, int N, typename R>
+__global__ void __launch_bounds__(Tile<D, N>::THREADS) vol_kernel(const VolArgs A) {
+  using T = Tile<D, N>;
+  using S = typename Arith<R>::S;
+  constexpr int ND = T::ND, NF = T::NF, NV = T::NV, EPB = T::EPB;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* sF = reinterpret_cast<R*>(smem_raw);  // [EPB][D][NV][ND]
+  const int el = threadIdx.x / ND, node = threadIdx.x - el * ND;
+  const int64_t e0 = (int64_t)blockIdx.x * EPB;
+  const int64_t e = e0 + el;
+  const bool active = e < A.m.ne;
+  const int64_t ne = A.m.ne;
+
+  int ix[3] = {node % N, (node / N) % N, node / (N * N)};
+  int ec[3] = {0, 0, 0};
+  if (active) elem_coords(A.m, e, ec);
+
+  // 1. stage input at this node and its pointwise fluxes
+  R u[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) u[v] = active ? R(A.in[((int64_t)v * ne + e) * ND + node]) : R(1.0);
+  {
+    R F[D][NV];
+    euler_flux_all<D, R>(u, R(A.gamma) - R(1.0), F);
+#pragma unroll
+    for (int d = 0; d < D; ++d)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) sF[((el * D + d) * NV + v) * ND + node] = F[d][v];
+  }
+  __syncthreads();
+
+  // 2. weak derivative (sum factorisation: one 1D contraction per direction) + face lift
+  R acc[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) acc[v] = R(0.0);
+  const S* fl = reinterpret_cast<const S*>(A.fl);
+  if (active) {
+    int stride = 1;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      const int base = node - ix[d] * stride;
+      const double* qrow = &A.tab->Q[d][ix[d] * N];
+#pragma unroll
+      for (int a = 0; a < N; ++a) {
+        R q = R(qrow[a]);
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+          acc[v] = r_fma(q, sF[((el * D + d) * NV + v) * ND + base + a * stride], acc[v]);
+      }
+      stride *= N;
+    }
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      const int j = face_index<D, N>(d, ix);
+      const int64_t elo = elem_shift(A.m, e, ec, d, -1);
+      R lp = R(A.tab->Lp[d][ix[d]]), lm = R(A.tab->Lm[d][ix[d]]);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        R fhi = Arith<R>::load(fl + ((int64_t)(d * NV + v) * ne + e) * NF + j);
+        R flo = Arith<R>::load(fl + ((int64_t)(d * NV + v) * ne + elo) * NF + j);
+        acc[v] = r_fma(lm, flo, acc[v]);
+        acc[v] = r_fma(-lp, fhi, acc[v]);
+      }
+    }
+  }
+
+  // 3. Runge-Kutta update in FP64; xnext = input of the next stage
+  R xnext[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const int64_t idx = ((int64_t)v * ne + e) * ND + node;
+    double k = Arith<R>::to_double(acc[v]);
+    double xn = 0.0;
+    if (active) {
+      if (A.mode == kModeRHS) {
+        A.x[idx] = k;
+      } else if (A.mode == kMode2R) {
+        double w0 = A.w[idx];
+        double w1 = fma(A.cb, k, w0);
+        A.w[idx] = w1;
+        if (!A.last) {
+          xn = fma(A.ca, k, w0);
+          A.x[idx] = xn;
+        } else {
+          xn = w1;
+        }
+      } else {
+        double w0 = A.w[idx];
+        double q0 = A.stage > 0 ? A.x[idx] : 0.0;
+        double q1 = fma(A.ca, q0, A.dt * k);
+        double w1 = fma(A.cb, q1, w0);
+        A.w[idx] = w1;
+        if (!A.last) A.x[idx] = q1;
+        xn = w1;
+      }
+    }
+    xnext[v] = R(xn);
+  }
+
+  // 4. traces of the next stage input
+  if (A.write_traces) {
+    __syncthreads();
+    R* sX = sF;  // reuse: [EPB][NV][ND]
+#pragma unroll
+    for (int v = 0; v < NV; ++v) sX[(el * NV + v) * ND + node] = xnext[v];
+    __syncthreads();
+    write_traces<D, N, R>(A.m, A.tab, sX, e0, reinterpret_cast<S*>(A.tr));
+  }
+}
+
+// Random-delay draw (same definition as the host schedule).
+__device__ __forceinline__ uint64_t splitmix64_dev(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+template <int D, int N, typename R>
+__global__ void __launch_bounds__(256) flux_kernel(const FluxArgs A) {
+  using S = typename Arith<R>::S;
+  constexpr int NF = IPow<N, D - 1>::value, NV = D + 2;
+  const int64_t ne = A.m.ne;
+  const int64_t per_dir = ne * NF;
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= D * per_dir) return;
+  const int d = (int)(g / per_dir);
+  const int64_t rem = g - d * per_dir;
+  const int64_t e = rem / NF;
+  const int j = (int)(rem - e * NF);
+  int ec[3];
+  elem_coords(A.m, e, ec);
+  const int64_t ehi = elem_shift(A.m, e, ec, d, +1);
+  const S* tr = reinterpret_cast<const S*>(A.tr);
+  R wm[NV], wp[NV], f[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    wm[v] = Arith<R>::load(tr + ((int64_t)((d * 2 + 1) * NV + v) * ne + e) * NF + j);
+    wp[v] = Arith<R>::load(tr + ((int64_t)((d * 2 + 0) * NV + v) * ne + ehi) * NF + j);
+  }
+  const R gamma = R(A.gamma);
+  const int slot = A.pe_mode ? A.pe_slot[(int64_t)d * ne + e] : -1;
+  if (slot < 0) {
+    llf_flux<D, R>(wm, wp, d, gamma, f);
+  } else {
+    S* ring = reinterpret_cast<S*>(A.ring);
+    const bool traces = (A.flux_kind == 3);
+    const int64_t lvl_stride = (int64_t)(traces ? 2 : 1) * NV * A.npe * NF;
+    int kt = A.uniform_delay;
+    if (A.random) {
+      const int iface = A.pe_iface[slot];
+      uint64_t ctr = (uint64_t)A.step * (uint64_t)A.n_iface + (uint64_t)iface;
+      kt = (int)(splitmix64_dev(A.seed ^ ctr) % (uint64_t)(A.dmax + 1));
+      const int64_t need = (A.nterms == 1) ? kt : kt + A.np;
+      if (A.step - need < 0) kt = 0;
+    }
+    if (A.store) {
+      S* dst = ring + (int64_t)A.head * lvl_stride;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        if (traces) {
+          Arith<R>::store(dst + ((int64_t)(0 * NV + v) * A.npe + slot) * NF + j, wm[v]);
+          Arith<R>::store(dst + ((int64_t)(1 * NV + v) * A.npe + slot) * NF + j, wp[v]);
+        }
+      }
+    }
+    if (kt == 0) {
+      llf_flux<D, R>(wm, wp, d, gamma, f);
+      if (A.store && !traces) {
+        S* dst = ring + (int64_t)A.head * lvl_stride;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) Arith<R>::store(dst + ((int64_t)v * A.npe + slot) * NF + j, f[v]);
+      }
+    } else {
+      if (A.store && !traces) {
+        R fr[NV];
+        llf_flux<D, R>(wm, wp, d, gamma, fr);
+        S* dst = ring + (int64_t)A.head * lvl_stride;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) Arith<R>::store(dst + ((int64_t)v * A.npe + slot) * NF + j, fr[v]);
+      }
+      const int off = A.random ? kt : 0;
+      R em[NV], ep[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) { em[v] = R(0.0); ep[v] = R(0.0); }
+      for (int l = 0; l < A.nterms; ++l) {
+        int lvl = A.head - off - l;
+        lvl %= A.depth;
+        if (lvl < 0) lvl += A.depth;
+        const R c = R(A.ctab[kt][l]);
+        const S* src = ring + (int64_t)lvl * lvl_stride;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          em[v] = r_fma(c, Arith<R>::load(src + ((int64_t)v * A.npe + slot) * NF + j), em[v]);
+          if (traces)
+            ep[v] = r_fma(c, Arith<R>::load(src + ((int64_t)(NV + v) * A.npe + slot) * NF + j), ep[v]);
+        }
+      }
+      if (traces) {
+        llf_flux<D, R>(em, ep, d, gamma, f);
+      } else {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) f[v] = em[v];
+      }
+    }
+  }
+  S* fl = reinterpret_cast<S*>(A.fl);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Arith<R>::store(fl + ((int64_t)(d * NV + v) * ne + e) * NF + j, f[v]);
+}
+
+// ------------------------------------------------------------------------------------
+// Launch helpers instantiated per arithmetic in the kernel translation units.
+// ------------------------------------------------------------------------------------
+template <int D, int N, typename R>
+cudaError_t launch_trace_t(const TraceArgs& a, cudaStream_t s) {
+  using T = Tile<D, N>;
+  int64_t blocks = (a.m.ne + T::EPB - 1) / T::EPB;
+  size_t smem = sizeof(R) * T::EPB * T::NV * T::ND;
+  trace_kernel<D, N, R><<<(unsigned)blocks, T::THREADS, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int D, int N, typename R>
+cudaError_t launch_vol_t(const VolArgs& a, cudaStream_t s) {
+  using T = Tile<D, N>;
+  int64_t blocks = (a.m.ne + T::EPB - 1) / T::EPB;
+  size_t smem = sizeof(R) * T::EPB * D * T::NV * T::ND;
+  if (smem > 48 * 1024) {
+    cudaError_t err = cudaFuncSetAttribute(vol_kernel<D, N, R>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+  }
+  vol_kernel<D, N, R><<<(unsigned)blocks, T::THREADS, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int D, int N, typename R>
+cudaError_t launch_flux_t(const FluxArgs& a, cudaStream_t s) {
+  constexpr int NF = IPow<N, D - 1>::value;
+  int64_t total = (int64_t)D * a.m.ne * NF;
+  int64_t blocks = (total + 255) / 256;
+  flux_kernel<D, N, R><<<(unsigned)blocks, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+// Dispatch over (dim, N) for one arithmetic R.
+template <typename R>
+struct Dispatch {
+  template <int D, int N>
+  static cudaError_t trace(const TraceArgs& a, cudaStream_t s) { return launch_trace_t<D, N, R>(a, s); }
+
+  static cudaError_t run_trace(int dim, int N, const TraceArgs& a, cudaStream_t s);
+  static cudaError_t run_flux(int dim, int N, const FluxArgs& a, cudaStream_t s);
+  static cudaError_t run_vol(int dim, int N, const VolArgs& a, cudaStream_t s);
+};
+
+#define ADG_DISPATCH_BODY(FN, ARGS)                                  \
+  if (dim == 2) {                                                    \
+    switch (N) {                                                     \
+      case 2: return FN<2, 2, R>(ARGS, s);                           \
+      case 3: return FN<2, 3, R>(ARGS, s);                           \
+      case 4: return FN<2, 4, R>(ARGS, s);                           \
+      case 5: return FN<2, 5, R>(ARGS, s);                           \
+      case 6: return FN<2, 6, R>(ARGS, s);                           \
+      case 7: return FN<2, 7, R>(ARGS, s);                           \
+      case 8: return FN<2, 8, R>(ARGS, s);                           \
+    }                                                                \
+  } else if (dim == 3) {                                             \
+    switch (N) {                                                     \
+      case 2: return FN<3, 2, R>(ARGS, s);                           \
+      case 3: return FN<3, 3, R>(ARGS, s);                           \
+      case 4: return FN<3, 4, R>(ARGS, s);                           \
+      case 5: return FN<3, 5, R>(ARGS, s);                           \
+      case 6: return FN<3, 6, R>(ARGS, s);                           \
+    }                                                                \
+  }                                                                  \
+  return cudaErrorInvalidValue;
+
+template <typename R>
+cudaError_t Dispatch<R>::run_trace(int dim, int N, const TraceArgs& a, cudaStream_t s) {
+  ADG_DISPATCH_BODY(launch_trace_t, a)
+}
+template <typename R>
+cudaError_t Dispatch<R>::run_flux(int dim, int N, const FluxArgs& a, cudaStream_t s) {
+  ADG_DISPATCH_BODY(launch_flux_t, a)
+}
+template <typename R>
+cudaError_t Dispatch<R>::run_vol(int dim, int N, const VolArgs& a, cudaStream_t s) {
+  ADG_DISPATCH_BODY(launch_vol_t, a)
+}
+
+}  // namespace adg

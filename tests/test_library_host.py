@@ -1,0 +1,100 @@
+"""CPU-side checks of the CUDA library: it loads, exports every declared symbol, and its
+host logic (basis, AT weights, RK tables, schedules) agrees with the oracle.  No GPU."""
+import re
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2603_28710_gb300 import adg
+from conftest import ROOT, golden
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2603_28710_gb300 import build
+    build.build()
+
+
+def test_library_exports_every_declared_symbol():
+    hdr = open(os.path.join(ROOT, "include", "adg.h")).read()
+    declared = set(re.findall(r"\b(adg_[a-z0-9_]+)\s*\(", hdr))
+    assert declared == set(adg.SYMBOLS)
+    L = adg.lib()
+    for name in declared:
+        assert hasattr(L, name), name
+
+
+@pytest.mark.parametrize("n", range(1, 10))
+def test_gauss_matches_oracle(n):
+    x, w = adg.host_gauss(n)
+    xo, wo = O.gauss(n)
+    np.testing.assert_allclose(x, xo, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(w, wo, rtol=0, atol=2e-15)
+
+
+@pytest.mark.parametrize("np_", range(0, 8))
+def test_at_weights_match_oracle(np_):
+    for km in (0.0, 0.14965902, 1.0, 2.632124764, 3.958, 7.0):
+        c = adg.host_at_coeffs(np_, km)
+        co = O.at_coeffs(np_, km)
+        np.testing.assert_allclose(c, co, rtol=1e-12, atol=1e-12 * np.abs(co).max())
+
+
+@pytest.mark.parametrize("scheme", ["rk22", "rk33", "ck45"])
+def test_rk_tables_match_oracle(scheme):
+    a, b, c = adg.host_rk(scheme)
+    ao, bo, co, _, _ = O.rk_tableau(scheme)
+    assert np.array_equal(b, bo)
+    if scheme == "ck45":
+        assert np.array_equal(a, ao)
+    else:
+        assert np.array_equal(a[:-1], ao[:-1])
+    np.testing.assert_allclose(c, co, rtol=0, atol=1e-15)
+
+
+SCHEDULES = [("sync", "caa", 1, 2), ("std", "caa", 1, 2), ("std", "caa", 3, 4), ("at", "caa", 0, 2),
+             ("at", "caa", 2, 2), ("at", "caa", 3, 4), ("at_trace", "caa", 4, 3), ("at", "caa", 10, 2)]
+
+
+@pytest.mark.parametrize("flux,mode,L,np_", SCHEDULES)
+def test_caa_schedule_bit_exact(flux, mode, L, np_):
+    for P, dim in (((2, 2), 2), ((8, 8), 2), ((2, 4, 2), 3)):
+        a = adg.host_schedule(flux, mode, L, np_, P, dim, 0, 0, 0, 200)
+        b = O.schedule(flux, mode, L, np_, P, dim, 0, 0, 0, 200)
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+        a2 = adg.host_schedule(flux, mode, L, np_, P, dim, 0, 0, 137, 50)
+        b2 = O.schedule(flux, mode, L, np_, P, dim, 0, 0, 137, 50)
+        for x, y in zip(a2, b2):
+            assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("flux", ["sync", "std", "at", "at_trace"])
+@pytest.mark.parametrize("dmax,seed", [(0, 1), (2, 20260301), (5, 7), (15, 2 ** 63 + 11)])
+def test_random_schedule_bit_exact(flux, dmax, seed):
+    for P, dim in (((8, 8), 2), ((2, 1), 2), ((2, 2, 2), 3)):
+        a = adg.host_schedule(flux, "random", 0, 3, P, dim, seed, dmax, 0, 120)
+        b = O.schedule(flux, "random", 0, 3, P, dim, seed, dmax, 0, 120)
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+
+
+def test_num_interfaces_match():
+    for dim, P in ((2, (1, 1)), (2, (8, 8)), (2, (4, 1)), (3, (8, 8, 8)), (3, (1, 2, 1))):
+        assert adg.host_num_interfaces(dim, P) == O.num_interfaces(dim, P)
+
+
+def test_dof_count_matches_table3():
+    # DoFs = nodes x variables (Table 3): N_E (N_p+1)^d (d+2) with N_p = 2
+    for row in golden("dof_table3.txt"):
+        dim, ne, dofs, tol = int(row[0]), int(row[2]), int(row[3]), int(row[4])
+        assert abs(ne * 3 ** dim * (dim + 2) - dofs) <= tol
+
+
+def test_bad_arguments_rejected_without_gpu():
+    with pytest.raises(adg.AdgError):
+        adg.host_gauss(0)
+    with pytest.raises(adg.AdgError):
+        adg.host_at_coeffs(9, 1.0)
