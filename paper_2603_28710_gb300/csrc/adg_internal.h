@@ -22,6 +22,12 @@ struct OpTables {
   double xe[kMaxN + 1];        // (N+1)-point Gauss nodes for error integrals
   double we[kMaxN + 1];
   double Le[(kMaxN + 1) * kMaxN];  // l_a(xe_p), entry [p*N + a]
+  // the same operator tables split into FP32 pairs (hi, lo) for the FP32 and pair kernels
+  float2 Qf[3][kMaxN * kMaxN];
+  float2 Lpf[3][kMaxN];
+  float2 Lmf[3][kMaxN];
+  float2 Tpf[kMaxN];
+  float2 Tmf[kMaxN];
 };
 
 struct MeshArgs {
@@ -36,6 +42,7 @@ struct VolArgs {
   MeshArgs m;
   const OpTables* tab;
   double gamma;
+  float2 gammaf;   // gamma as an FP32 pair
   int mode;        // UpdateMode
   int stage, last; // stage index; last = 1 on the final stage of a step
   double ca, cb;   // 2R: dt*a_m, dt*b_m ; 2N: A_m, B_m
@@ -51,6 +58,7 @@ struct VolArgs {
 struct FluxArgs {
   MeshArgs m;
   double gamma;
+  float2 gammaf;
   const void* tr;
   void* fl;
   // subdomain-face handling
@@ -69,6 +77,7 @@ struct FluxArgs {
   int64_t step;
   int n_iface, dmax, np;
   double ctab[kMaxCoefDelay][kMaxN];  // AT weights per delay for this stage
+  float2 ctabf[kMaxCoefDelay][kMaxN]; // the same as FP32 pairs
 };
 
 struct TraceArgs {

@@ -1,7 +1,10 @@
-// Arithmetic layer of the operator kernels: storage type, loads/stores and the few math
-// functions the Euler flux needs, for each arithmetic type R.
+// Arithmetic layer of the operator kernels: storage type, conversions, table access,
+// dot-product accumulators and the few math functions the Euler flux needs, for each
+// operator arithmetic R (double, float, df64).
 #pragma once
 #include <cuda_runtime.h>
+
+#include "df64.cuh"
 
 namespace adg {
 
@@ -10,18 +13,43 @@ struct Arith;
 
 template <>
 struct Arith<double> {
-  using S = double;
+  using S = double;   // storage of traces / fluxes / ring entries
+  using Acc = double; // dot-product accumulator
   __device__ static __forceinline__ double load(const double* p) { return __ldg(p); }
   __device__ static __forceinline__ void store(double* p, double v) { *p = v; }
   __device__ static __forceinline__ double to_double(double v) { return v; }
+  __device__ static __forceinline__ double from_double(double v) { return v; }
+  __device__ static __forceinline__ double tab(const double* d, const float2*, int i) { return d[i]; }
+  __device__ static __forceinline__ double pair(double d, float2) { return d; }
 };
 
 template <>
 struct Arith<float> {
   using S = float;
+  using Acc = float;
   __device__ static __forceinline__ float load(const float* p) { return __ldg(p); }
   __device__ static __forceinline__ void store(float* p, float v) { *p = v; }
   __device__ static __forceinline__ double to_double(float v) { return (double)v; }
+  __device__ static __forceinline__ float from_double(double v) { return __double2float_rn(v); }
+  __device__ static __forceinline__ float tab(const double*, const float2* f, int i) { return f[i].x; }
+  __device__ static __forceinline__ float pair(double, float2 f) { return f.x; }
+};
+
+template <>
+struct Arith<df64> {
+  using S = float2;
+  using Acc = df64acc;
+  __device__ static __forceinline__ df64 load(const float2* p) {
+    float2 v = __ldg(p);
+    return df64(v.x, v.y);
+  }
+  __device__ static __forceinline__ void store(float2* p, df64 v) { *p = make_float2(v.hi, v.lo); }
+  __device__ static __forceinline__ double to_double(df64 v) { return (double)v.hi + (double)v.lo; }
+  __device__ static __forceinline__ df64 from_double(double v) { return df64(v); }
+  __device__ static __forceinline__ df64 tab(const double*, const float2* f, int i) {
+    return df64(f[i].x, f[i].y);
+  }
+  __device__ static __forceinline__ df64 pair(double, float2 f) { return df64(f.x, f.y); }
 };
 
 __device__ __forceinline__ double r_rcp(double x) { return 1.0 / x; }
@@ -32,5 +60,13 @@ __device__ __forceinline__ double r_max(double a, double b) { return fmax(a, b);
 __device__ __forceinline__ float r_max(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ double r_fma(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float r_fma(float a, float b, float c) { return fmaf(a, b, c); }
+
+// accumulators: plain FMA chains for the native types
+__device__ __forceinline__ double acc_zero(double) { return 0.0; }
+__device__ __forceinline__ float acc_zero(float) { return 0.0f; }
+__device__ __forceinline__ double acc_fma(double a, double b, double t) { return fma(a, b, t); }
+__device__ __forceinline__ float acc_fma(float a, float b, float t) { return fmaf(a, b, t); }
+__device__ __forceinline__ double acc_result(double t) { return t; }
+__device__ __forceinline__ float acc_result(float t) { return t; }
 
 }  // namespace adg

@@ -1,0 +1,138 @@
+// FP32-pair ("double-word") arithmetic for the operator kernels.
+//
+// A value is hi + lo with |lo| <= ulp(hi)/2, about 48 significant bits.  GB300 issues
+// FP32 FMAs at about 62x the FP64 rate, so an operator written in this arithmetic runs
+// faster than native FP64 while staying within a few units of 2^-48 of it.  Building
+// blocks, all from the published error-free transformations:
+//   TwoSum (Knuth, TAOCP vol. 2): s + e == a + b exactly, 6 flops, no ordering assumption;
+//   FastTwoSum (Dekker 1971): same when |a| >= |b|, 3 flops;
+//   TwoProd with FMA: p + e == a * b exactly, 2 flops;
+//   double-word add / multiply: the accurate algorithms of Joldes, Muller & Popescu,
+//     "Tight and rigorous error bounds for basic building blocks of double-word
+//     arithmetic", ACM TOMS 44(2), 2017 (relative error <= 3u^2 and 4u^2, u = 2^-24);
+//   reciprocal and square root: an FP32 seed refined by one Newton step carried out in
+//     double-word arithmetic (error of order u^2);
+//   dot products: a compensated accumulator in the style of Dot2 (Ogita, Rump & Oishi,
+//     SIAM J. Sci. Comput. 26(6), 2005): the exact FP32 product and sum errors are
+//     gathered in a second FP32 word, so a sum of n products carries an error of about
+//     n u^2 sum |a_i b_i| instead of n u sum |a_i b_i|.
+// The compiler must not reassociate FP32 operations here (no fast-math flags).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace adg {
+
+struct df64 {
+  float hi, lo;
+  __device__ __forceinline__ df64() {}
+  __device__ __forceinline__ df64(float h, float l) : hi(h), lo(l) {}
+  // exact split of an FP64 value into hi + lo (lo rounded: total error <= 2^-48 |x|)
+  __device__ __forceinline__ explicit df64(double x) {
+    hi = __double2float_rn(x);
+    lo = __double2float_rn(x - (double)hi);
+  }
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  float bp = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+}
+
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = __fmul_rn(a, b);
+  e = __fmaf_rn(a, b, -p);
+}
+
+// accurate double-word + double-word
+__device__ __forceinline__ df64 operator+(df64 x, df64 y) {
+  float sh, sl, th, tl, vh, vl, zh, zl;
+  two_sum(x.hi, y.hi, sh, sl);
+  two_sum(x.lo, y.lo, th, tl);
+  float c = __fadd_rn(sl, th);
+  fast_two_sum(sh, c, vh, vl);
+  float w = __fadd_rn(tl, vl);
+  fast_two_sum(vh, w, zh, zl);
+  return df64(zh, zl);
+}
+
+__device__ __forceinline__ df64 operator-(df64 x) { return df64(-x.hi, -x.lo); }
+__device__ __forceinline__ df64 operator-(df64 x, df64 y) { return x + (-y); }
+
+// double-word * double-word with FMA
+__device__ __forceinline__ df64 operator*(df64 x, df64 y) {
+  float ch, cl1;
+  two_prod(x.hi, y.hi, ch, cl1);
+  float tl0 = __fmul_rn(x.lo, y.lo);
+  float tl1 = __fmaf_rn(x.hi, y.lo, tl0);
+  float cl2 = __fmaf_rn(x.lo, y.hi, tl1);
+  float cl3 = __fadd_rn(cl1, cl2);
+  float zh, zl;
+  fast_two_sum(ch, cl3, zh, zl);
+  return df64(zh, zl);
+}
+
+// multiplication by a power of two is exact
+__device__ __forceinline__ df64 scale_pow2(df64 x, float p2) { return df64(x.hi * p2, x.lo * p2); }
+
+__device__ __forceinline__ df64 r_rcp(df64 y) {
+  // r0 ~ 1/y.hi; e = 1 - y r0 (fma keeps it exact up to the lo term); r = r0 + r0 e
+  float r0 = __frcp_rn(y.hi);
+  float e = __fmaf_rn(-y.hi, r0, 1.0f);
+  e = __fmaf_rn(-y.lo, r0, e);
+  float zh, zl;
+  fast_two_sum(r0, __fmul_rn(r0, e), zh, zl);
+  return df64(zh, zl);
+}
+
+__device__ __forceinline__ df64 r_sqrt(df64 x) {
+  if (x.hi <= 0.0f) return df64(0.0f, 0.0f);
+  // s0 = sqrt(x.hi) rounded; residual x - s0^2 exactly enough; s = s0 + res / (2 s0)
+  float s0 = __fsqrt_rn(x.hi);
+  float ph, pl;
+  two_prod(s0, s0, ph, pl);
+  float res = __fadd_rn(__fsub_rn(__fsub_rn(x.hi, ph), pl), x.lo);
+  float corr = __fdividef(res, 2.0f * s0);
+  float zh, zl;
+  fast_two_sum(s0, corr, zh, zl);
+  return df64(zh, zl);
+}
+
+__device__ __forceinline__ bool operator>(df64 a, df64 b) {
+  return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo);
+}
+__device__ __forceinline__ df64 r_max(df64 a, df64 b) { return (b > a) ? b : a; }
+__device__ __forceinline__ df64 r_fma(df64 a, df64 b, df64 c) { return a * b + c; }
+
+// Compensated sum of products: value = s + c (unnormalised).
+struct df64acc {
+  float s, c;
+};
+__device__ __forceinline__ df64acc acc_zero(df64acc) { return df64acc{0.0f, 0.0f}; }
+__device__ __forceinline__ df64acc acc_fma(df64 a, df64 b, df64acc t) {
+  float p, pe, s, se;
+  two_prod(a.hi, b.hi, p, pe);
+  two_sum(t.s, p, s, se);
+  float c = __fadd_rn(t.c, __fadd_rn(se, pe));
+  c = __fmaf_rn(a.hi, b.lo, c);
+  c = __fmaf_rn(a.lo, b.hi, c);
+  return df64acc{s, c};
+}
+__device__ __forceinline__ df64acc acc_add(df64 a, df64acc t) {
+  float s, se;
+  two_sum(t.s, a.hi, s, se);
+  return df64acc{s, __fadd_rn(t.c, __fadd_rn(se, a.lo))};
+}
+__device__ __forceinline__ df64 acc_result(df64acc t) {
+  float zh, zl;
+  two_sum(t.s, t.c, zh, zl);
+  return df64(zh, zl);
+}
+
+}  // namespace adg

@@ -9,20 +9,24 @@ cudaError_t launch_vol_fp64(int, int, const VolArgs&, cudaStream_t);
 cudaError_t launch_trace_fp32(int, int, const TraceArgs&, cudaStream_t);
 cudaError_t launch_flux_fp32(int, int, const FluxArgs&, cudaStream_t);
 cudaError_t launch_vol_fp32(int, int, const VolArgs&, cudaStream_t);
+cudaError_t launch_trace_df64(int, int, const TraceArgs&, cudaStream_t);
+cudaError_t launch_flux_df64(int, int, const FluxArgs&, cudaStream_t);
+cudaError_t launch_vol_df64(int, int, const VolArgs&, cudaStream_t);
 
 bool kernels_available(int prec, int dim, int N) {
-  if (prec != 0 && prec != 1) return false;
+  if (prec < 0 || prec > 2) return false;
   if (dim == 2) return N >= 2 && N <= 8;
   if (dim == 3) return N >= 2 && N <= 6;
   return false;
 }
 
-size_t storage_bytes(int prec) { return prec == 1 ? sizeof(float) : sizeof(double); }
+size_t storage_bytes(int prec) { return prec == 1 ? sizeof(float) : (prec == 2 ? sizeof(float2) : sizeof(double)); }
 
 cudaError_t launch_trace(int prec, int dim, int N, const TraceArgs& a, cudaStream_t s) {
   switch (prec) {
     case 0: return launch_trace_fp64(dim, N, a, s);
     case 1: return launch_trace_fp32(dim, N, a, s);
+    case 2: return launch_trace_df64(dim, N, a, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -31,6 +35,7 @@ cudaError_t launch_flux(int prec, int dim, int N, const FluxArgs& a, cudaStream_
   switch (prec) {
     case 0: return launch_flux_fp64(dim, N, a, s);
     case 1: return launch_flux_fp32(dim, N, a, s);
+    case 2: return launch_flux_df64(dim, N, a, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -39,6 +44,7 @@ cudaError_t launch_vol(int prec, int dim, int N, const VolArgs& a, cudaStream_t 
   switch (prec) {
     case 0: return launch_vol_fp64(dim, N, a, s);
     case 1: return launch_vol_fp32(dim, N, a, s);
+    case 2: return launch_vol_df64(dim, N, a, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -83,6 +83,13 @@ adg_status cuda_fail(adg_solver* s, cudaError_t e, const char* what) {
     if (e__ != cudaSuccess) return cuda_fail((S), e__, #call); \
   } while (0)
 
+// (hi, lo) FP32 pair of a value: hi = RN(v), lo = RN(v - hi)
+float2 split2(long double v) {
+  float hi = (float)v;
+  float lo = (float)(v - (long double)hi);
+  return make_float2(hi, lo);
+}
+
 // ---- basis (Gauss-Legendre, Lagrange, barycentric derivative) -----------------------
 
 // Legendre P_n and P_n' by the three-term recurrence and P_k' = k P_{k-1} + x P_{k-1}'.
@@ -176,15 +183,23 @@ void build_tables(adg_solver* s) {
   for (int d = 0; d < 3; ++d) {
     long double sc = 2.0L / (long double)s->h[d];
     for (int i = 0; i < N; ++i) {
-      for (int a = 0; a < N; ++a)
-        T.Q[d][i * N + a] = (double)(sc * (long double)wd[a] * Dm[a][i] / (long double)wd[i]);
-      T.Lp[d][i] = (double)(sc * lp[i] / (long double)wd[i]);
-      T.Lm[d][i] = (double)(sc * lm[i] / (long double)wd[i]);
+      for (int a = 0; a < N; ++a) {
+        long double q = sc * (long double)wd[a] * Dm[a][i] / (long double)wd[i];
+        T.Q[d][i * N + a] = (double)q;
+        T.Qf[d][i * N + a] = split2(q);
+      }
+      long double vp = sc * lp[i] / (long double)wd[i], vm = sc * lm[i] / (long double)wd[i];
+      T.Lp[d][i] = (double)vp;
+      T.Lm[d][i] = (double)vm;
+      T.Lpf[d][i] = split2(vp);
+      T.Lmf[d][i] = split2(vm);
     }
   }
   for (int a = 0; a < N; ++a) {
     T.Tp[a] = (double)lp[a];
     T.Tm[a] = (double)lm[a];
+    T.Tpf[a] = split2(lp[a]);
+    T.Tmf[a] = split2(lm[a]);
   }
   double xe[16], we[16];
   gauss_legendre(N + 1, xe, we);
@@ -198,13 +213,19 @@ void build_tables(adg_solver* s) {
 }
 
 // ---- AT weights: Lagrange extrapolation to the stage time from levels -(km + l) ------
-void at_weights(int np, double km, double* c) {
+void at_weights_ld(int np, long double km, long double* c) {
   for (int l = 0; l <= np; ++l) {
     long double v = 1.0L;
     for (int j = 0; j <= np; ++j)
-      if (j != l) v *= ((long double)km + j) / (long double)(j - l);
-    c[l] = (double)v;
+      if (j != l) v *= (km + j) / (long double)(j - l);
+    c[l] = v;
   }
+}
+
+void at_weights(int np, double km, double* c) {
+  long double t[kMaxN];
+  at_weights_ld(np, km, t);
+  for (int l = 0; l <= np; ++l) c[l] = (double)t[l];
 }
 
 // ---- Runge-Kutta coefficients ---------------------------------------------------------
@@ -369,6 +390,7 @@ FluxArgs base_flux_args(adg_solver* s) {
   std::memset(&fa, 0, sizeof(fa));
   fa.m = s->margs;
   fa.gamma = s->opt.gamma;
+  fa.gammaf = split2(s->opt.gamma);
   fa.tr = s->tr;
   fa.fl = s->fl;
   fa.flux_kind = (int)s->flux;
@@ -658,8 +680,14 @@ adg_status adg_step(adg_solver* s, int n_steps) {
         for (int kt = 0; kt <= kmax && kt < kMaxCoefDelay; ++kt) {
           if (s->flux == ADG_FLUX_STD_DELAYED) {
             fa.ctab[kt][0] = 1.0;
+            fa.ctabf[kt][0] = make_float2(1.0f, 0.0f);
           } else {
-            at_weights(s->np, kt + s->rkc[m], fa.ctab[kt]);
+            long double c[kMaxN];
+            at_weights_ld(s->np, (long double)kt + s->rkc[m], c);
+            for (int l = 0; l <= s->np; ++l) {
+              fa.ctab[kt][l] = (double)c[l];
+              fa.ctabf[kt][l] = split2(c[l]);
+            }
           }
         }
       }
@@ -671,6 +699,7 @@ adg_status adg_step(adg_solver* s, int n_steps) {
       va.m = s->margs;
       va.tab = s->tab_dev;
       va.gamma = s->opt.gamma;
+      va.gammaf = split2(s->opt.gamma);
       va.mode = s->rk2n ? kMode2N : kMode2R;
       va.stage = m;
       va.last = (m == s->stages - 1);
@@ -733,6 +762,7 @@ adg_status adg_rhs(adg_solver* s, const double* u, double* k, int64_t count, int
   va.m = s->margs;
   va.tab = s->tab_dev;
   va.gamma = s->opt.gamma;
+  va.gammaf = split2(s->opt.gamma);
   va.mode = kModeRHS;
   va.in = ud;
   va.x = kd;

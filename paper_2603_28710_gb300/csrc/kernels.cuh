@@ -59,13 +59,13 @@ template <int D, typename R>
 __device__ __forceinline__ void euler_flux_all(const R* w, R gm1, R (*F)[D + 2]) {
   R irho = r_rcp(w[0]);
   R u[D];
-  R kin2 = R(0.0);
+  R kin2 = R(0.0f);
 #pragma unroll
   for (int d = 0; d < D; ++d) {
     u[d] = w[1 + d] * irho;
     kin2 = r_fma(w[1 + d], u[d], kin2);
   }
-  R p = gm1 * (w[D + 1] - R(0.5) * kin2);
+  R p = gm1 * (w[D + 1] - R(0.5f) * kin2);
   R ep = w[D + 1] + p;
 #pragma unroll
   for (int d = 0; d < D; ++d) {
@@ -81,7 +81,7 @@ __device__ __forceinline__ void euler_flux_all(const R* w, R gm1, R (*F)[D + 2])
 template <int D, typename R>
 __device__ __forceinline__ void llf_flux(const R* wm, const R* wp, int d, R gamma, R* f) {
   constexpr int NV = D + 2;
-  R gm1 = gamma - R(1.0);
+  R gm1 = gamma - R(1.0f);
   R s2[2];
   R fd[2][NV];
   const R* ws[2] = {wm, wp};
@@ -89,7 +89,7 @@ __device__ __forceinline__ void llf_flux(const R* wm, const R* wp, int d, R gamm
   for (int side = 0; side < 2; ++side) {
     const R* w = ws[side];
     R irho = r_rcp(w[0]);
-    R u2 = R(0.0), kin2 = R(0.0), ud = R(0.0);
+    R u2 = R(0.0f), kin2 = R(0.0f), ud = R(0.0f);
 #pragma unroll
     for (int c = 0; c < D; ++c) {
       R uc = w[1 + c] * irho;
@@ -97,7 +97,7 @@ __device__ __forceinline__ void llf_flux(const R* wm, const R* wp, int d, R gamm
       kin2 = r_fma(w[1 + c], uc, kin2);
       if (c == d) ud = uc;
     }
-    R p = gm1 * (w[D + 1] - R(0.5) * kin2);
+    R p = gm1 * (w[D + 1] - R(0.5f) * kin2);
     s2[side] = u2 + gamma * p * irho;
     fd[side][0] = w[1 + d];
 #pragma unroll
@@ -105,10 +105,10 @@ __device__ __forceinline__ void llf_flux(const R* wm, const R* wp, int d, R gamm
     fd[side][1 + d] = fd[side][1 + d] + p;
     fd[side][D + 1] = (w[D + 1] + p) * ud;
   }
-  R lam = R(0.5) * r_sqrt(r_max(s2[0], s2[1]));
-  R hl = R(0.5) * lam;
+  R lam = R(0.5f) * r_sqrt(r_max(s2[0], s2[1]));
+  R hl = R(0.5f) * lam;
 #pragma unroll
-  for (int v = 0; v < NV; ++v) f[v] = R(0.5) * (fd[0][v] + fd[1][v]) + hl * (wm[v] - wp[v]);
+  for (int v = 0; v < NV; ++v) f[v] = R(0.5f) * (fd[0][v] + fd[1][v]) + hl * (wm[v] - wp[v]);
 }
 
 // Transverse coordinates of face node j of a face normal to d -> base node index of the
@@ -160,10 +160,12 @@ __device__ __forceinline__ void write_traces(const MeshArgs& m, const OpTables* 
     int stride = 1;
     for (int c = 0; c < d; ++c) stride *= N;
     const double* tw = side ? tab->Tp : tab->Tm;
-    R acc = R(0.0);
+    const float2* twf = side ? tab->Tpf : tab->Tmf;
+    typename Arith<R>::Acc acc = acc_zero(typename Arith<R>::Acc());
 #pragma unroll
-    for (int a = 0; a < N; ++a) acc = r_fma(R(tw[a]), sX[(el * NV + v) * ND + base + a * stride], acc);
-    Arith<R>::store(tr + ((int64_t)(ds * NV + v) * m.ne + e) * NF + j, acc);
+    for (int a = 0; a < N; ++a)
+      acc = acc_fma(Arith<R>::tab(tw, twf, a), sX[(el * NV + v) * ND + base + a * stride], acc);
+    Arith<R>::store(tr + ((int64_t)(ds * NV + v) * m.ne + e) * NF + j, acc_result(acc));
   }
 }
 
@@ -178,7 +180,8 @@ __global__ void __launch_bounds__(Tile<D, N>::THREADS) trace_kernel(const TraceA
   const int64_t e = e0 + el;
   if (e < A.m.ne) {
 #pragma unroll
-    for (int v = 0; v < NV; ++v) sX[(el * NV + v) * ND + node] = R(A.u[((int64_t)v * A.m.ne + e) * ND + node]);
+    for (int v = 0; v < NV; ++v)
+      sX[(el * NV + v) * ND + node] = Arith<R>::from_double(A.u[((int64_t)v * A.m.ne + e) * ND + node]);
   }
   __syncthreads();
   write_traces<D, N, R>(A.m, A.tab, sX, e0, reinterpret_cast<typename Arith<R>::S*>(A.tr));
@@ -204,10 +207,11 @@ __global__ void __launch_bounds__(Tile<D, N>::THREADS) vol_kernel(const VolArgs 
   // 1. stage input at this node and its pointwise fluxes
   R u[NV];
 #pragma unroll
-  for (int v = 0; v < NV; ++v) u[v] = active ? R(A.in[((int64_t)v * ne + e) * ND + node]) : R(1.0);
+  for (int v = 0; v < NV; ++v)
+    u[v] = active ? Arith<R>::from_double(A.in[((int64_t)v * ne + e) * ND + node]) : R(1.0f);
   {
     R F[D][NV];
-    euler_flux_all<D, R>(u, R(A.gamma) - R(1.0), F);
+    euler_flux_all<D, R>(u, Arith<R>::pair(A.gamma, A.gammaf) - R(1.0f), F);
 #pragma unroll
     for (int d = 0; d < D; ++d)
 #pragma unroll
@@ -216,22 +220,22 @@ __global__ void __launch_bounds__(Tile<D, N>::THREADS) vol_kernel(const VolArgs 
   __syncthreads();
 
   // 2. weak derivative (sum factorisation: one 1D contraction per direction) + face lift
-  R acc[NV];
+  using Acc = typename Arith<R>::Acc;
+  Acc acc[NV];
 #pragma unroll
-  for (int v = 0; v < NV; ++v) acc[v] = R(0.0);
+  for (int v = 0; v < NV; ++v) acc[v] = acc_zero(Acc());
   const S* fl = reinterpret_cast<const S*>(A.fl);
   if (active) {
     int stride = 1;
 #pragma unroll
     for (int d = 0; d < D; ++d) {
       const int base = node - ix[d] * stride;
-      const double* qrow = &A.tab->Q[d][ix[d] * N];
 #pragma unroll
       for (int a = 0; a < N; ++a) {
-        R q = R(qrow[a]);
+        const R q = Arith<R>::tab(A.tab->Q[d], A.tab->Qf[d], ix[d] * N + a);
 #pragma unroll
         for (int v = 0; v < NV; ++v)
-          acc[v] = r_fma(q, sF[((el * D + d) * NV + v) * ND + base + a * stride], acc[v]);
+          acc[v] = acc_fma(q, sF[((el * D + d) * NV + v) * ND + base + a * stride], acc[v]);
       }
       stride *= N;
     }
@@ -239,13 +243,14 @@ __global__ void __launch_bounds__(Tile<D, N>::THREADS) vol_kernel(const VolArgs 
     for (int d = 0; d < D; ++d) {
       const int j = face_index<D, N>(d, ix);
       const int64_t elo = elem_shift(A.m, e, ec, d, -1);
-      R lp = R(A.tab->Lp[d][ix[d]]), lm = R(A.tab->Lm[d][ix[d]]);
+      const R lp = Arith<R>::tab(A.tab->Lp[d], A.tab->Lpf[d], ix[d]);
+      const R lm = Arith<R>::tab(A.tab->Lm[d], A.tab->Lmf[d], ix[d]);
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         R fhi = Arith<R>::load(fl + ((int64_t)(d * NV + v) * ne + e) * NF + j);
         R flo = Arith<R>::load(fl + ((int64_t)(d * NV + v) * ne + elo) * NF + j);
-        acc[v] = r_fma(lm, flo, acc[v]);
-        acc[v] = r_fma(-lp, fhi, acc[v]);
+        acc[v] = acc_fma(lm, flo, acc[v]);
+        acc[v] = acc_fma(-lp, fhi, acc[v]);
       }
     }
   }
@@ -255,7 +260,7 @@ __global__ void __launch_bounds__(Tile<D, N>::THREADS) vol_kernel(const VolArgs 
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     const int64_t idx = ((int64_t)v * ne + e) * ND + node;
-    double k = Arith<R>::to_double(acc[v]);
+    double k = Arith<R>::to_double(acc_result(acc[v]));
     double xn = 0.0;
     if (active) {
       if (A.mode == kModeRHS) {
@@ -280,7 +285,7 @@ __global__ void __launch_bounds__(Tile<D, N>::THREADS) vol_kernel(const VolArgs 
         xn = w1;
       }
     }
-    xnext[v] = R(xn);
+    xnext[v] = Arith<R>::from_double(xn);
   }
 
   // 4. traces of the next stage input
@@ -324,7 +329,7 @@ __global__ void __launch_bounds__(256) flux_kernel(const FluxArgs A) {
     wm[v] = Arith<R>::load(tr + ((int64_t)((d * 2 + 1) * NV + v) * ne + e) * NF + j);
     wp[v] = Arith<R>::load(tr + ((int64_t)((d * 2 + 0) * NV + v) * ne + ehi) * NF + j);
   }
-  const R gamma = R(A.gamma);
+  const R gamma = Arith<R>::pair(A.gamma, A.gammaf);
   const int slot = A.pe_mode ? A.pe_slot[(int64_t)d * ne + e] : -1;
   if (slot < 0) {
     llf_flux<D, R>(wm, wp, d, gamma, f);
@@ -366,27 +371,31 @@ __global__ void __launch_bounds__(256) flux_kernel(const FluxArgs A) {
         for (int v = 0; v < NV; ++v) Arith<R>::store(dst + ((int64_t)v * A.npe + slot) * NF + j, fr[v]);
       }
       const int off = A.random ? kt : 0;
-      R em[NV], ep[NV];
+      using Acc = typename Arith<R>::Acc;
+      Acc am[NV], ap[NV];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) { em[v] = R(0.0); ep[v] = R(0.0); }
+      for (int v = 0; v < NV; ++v) { am[v] = acc_zero(Acc()); ap[v] = acc_zero(Acc()); }
       for (int l = 0; l < A.nterms; ++l) {
         int lvl = A.head - off - l;
         lvl %= A.depth;
         if (lvl < 0) lvl += A.depth;
-        const R c = R(A.ctab[kt][l]);
+        const R c = Arith<R>::pair(A.ctab[kt][l], A.ctabf[kt][l]);
         const S* src = ring + (int64_t)lvl * lvl_stride;
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          em[v] = r_fma(c, Arith<R>::load(src + ((int64_t)v * A.npe + slot) * NF + j), em[v]);
+          am[v] = acc_fma(c, Arith<R>::load(src + ((int64_t)v * A.npe + slot) * NF + j), am[v]);
           if (traces)
-            ep[v] = r_fma(c, Arith<R>::load(src + ((int64_t)(NV + v) * A.npe + slot) * NF + j), ep[v]);
+            ap[v] = acc_fma(c, Arith<R>::load(src + ((int64_t)(NV + v) * A.npe + slot) * NF + j), ap[v]);
         }
       }
       if (traces) {
+        R em[NV], ep[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) { em[v] = acc_result(am[v]); ep[v] = acc_result(ap[v]); }
         llf_flux<D, R>(em, ep, d, gamma, f);
       } else {
 #pragma unroll
-        for (int v = 0; v < NV; ++v) f[v] = em[v];
+        for (int v = 0; v < NV; ++v) f[v] = acc_result(am[v]);
       }
     }
   }
