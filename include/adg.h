@@ -179,6 +179,38 @@ adg_status adg_check_finite(adg_solver* s);
 adg_status adg_set_profiling(adg_solver* s, int enable);
 adg_status adg_get_profile(adg_solver* s, double* ms, int64_t* launches);
 
+/* ---- operator without device allocation ------------------------------------------ */
+
+/* Size of the built-in device scratch array used by adg_rhs_noalloc (32 MiB). */
+#define ADG_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* The synchronous FP64 operator k = M^{-1} L_h(u) of adg_rhs, for callers that cannot
+ * allocate device memory: a host application that owns the whole device memory budget
+ * (a fixed arena or pool that forbids outside allocations), or a loop where the implicit
+ * device synchronisation and unbounded latency of cudaMalloc are not acceptable.  The
+ * paper has no counterpart; this is a library convenience.
+ *
+ * Needs no handle and allocates nothing: no cudaMalloc, no cudaFree, no allocating
+ * library routine.  Its scratch (operator tables, face traces, face fluxes) sits in one
+ * file-scope device array of ADG_NOALLOC_SCRATCH_BYTES that every GPU loading the library
+ * holds until the process exits.  The first call on a device looks up that array's
+ * device address (cudaGetSymbolAddress, with the device current); make that first call
+ * before any stream capture.  Every call overwrites all the scratch it later reads, so
+ * nothing carries over between calls; calls that overlap on the GPU (two streams, two
+ * host threads) share the one array and race.
+ *   mesh, degree: as in adg_create (periodic uniform mesh; degree 1..7 in 2D, 1..5 in 3D);
+ *   gamma:        ratio of specific heats (> 1);
+ *   u, k:         DEVICE pointers, n_dof = (dim+2) * n_elements * (degree+1)^dim values each,
+ *                 layout as for adg_set_state; u is read, k written;
+ *   count:        must equal n_dof;
+ *   cuda_stream:  cudaStream_t the work is ordered on (NULL = legacy default stream).
+ * The call enqueues the work and returns without waiting.  A mesh whose scratch
+ * (2 d + d) (d+2) n_elements (degree+1)^(d-1) doubles plus the tables exceeds
+ * ADG_NOALLOC_SCRATCH_BYTES is rejected with ADG_ERR_INVALID; adg_last_error(NULL) says
+ * how many bytes it needed.  Other errors: ADG_ERR_INVALID (arguments), ADG_ERR_CUDA. */
+adg_status adg_rhs_noalloc(const adg_mesh* mesh, int degree, double gamma, const double* u,
+                           double* k, int64_t count, void* cuda_stream);
+
 /* Message for the last failing call on s (NULL: on this thread, for calls without a
  * handle).  Valid until the next call on the same handle/thread. */
 const char* adg_last_error(const adg_solver* s);

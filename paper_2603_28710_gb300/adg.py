@@ -27,7 +27,7 @@ STATUS = {0: "ADG_OK", 1: "ADG_ERR_INVALID", 2: "ADG_ERR_UNSUPPORTED", 3: "ADG_E
 SYMBOLS = ["adg_default_options", "adg_create", "adg_set_state", "adg_init_vortex",
            "adg_init_tgv", "adg_step", "adg_get_state", "adg_rhs", "adg_get_schedule",
            "adg_info", "adg_conservation", "adg_l2_error_vortex", "adg_check_finite",
-           "adg_last_error", "adg_destroy", "adg_set_profiling", "adg_get_profile", "adg_host_gauss", "adg_host_at_coeffs",
+           "adg_last_error", "adg_destroy", "adg_set_profiling", "adg_get_profile", "adg_rhs_noalloc", "adg_host_gauss", "adg_host_at_coeffs",
            "adg_host_rk", "adg_host_schedule", "adg_host_num_interfaces"]
 
 
@@ -83,6 +83,7 @@ def lib():
             "adg_destroy": ([P], None),
             "adg_set_profiling": ([P, I], I),
             "adg_get_profile": ([P, P, P], I),
+            "adg_rhs_noalloc": ([ctypes.POINTER(Mesh), I, D, P, P, I64, P], I),
             "adg_host_gauss": ([I, P, P], I),
             "adg_host_at_coeffs": ([I, D, P], I),
             "adg_host_rk": ([I, P, P, P, P], I),
@@ -162,6 +163,26 @@ def host_schedule(flux, delay_mode, max_delay, np_, P, dim, seed, dmax, n0, coun
                                    seed & 0xFFFFFFFFFFFFFFFF, dmax, n0, count, _np_ptr(comm),
                                    _np_ptr(k), _np_ptr(dl)))
     return comm, k, dl[:, :nif]
+
+
+def rhs_noalloc(dim, n_elem, degree, u, k, lo=None, hi=None, gamma=1.4, stream=None):
+    """adg_rhs_noalloc on CUDA torch tensors u (read) and k (written); no allocation."""
+    lo = lo if lo is not None else ((-5.0,) * dim)
+    hi = hi if hi is not None else ((5.0,) * dim)
+    m = Mesh()
+    m.dim = dim
+    for i in range(3):
+        m.n_elem[i] = n_elem[i] if i < dim else 1
+        m.lo[i] = lo[i] if i < dim else 0.0
+        m.hi[i] = hi[i] if i < dim else 1.0
+    pu, n, du = _buf(u)
+    pk, nk, dk = _buf(k, writable=True)
+    if not (du and dk) or n != nk:
+        raise ValueError("u and k must be CUDA tensors of the same size")
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    _check(lib().adg_rhs_noalloc(ctypes.byref(m), degree, gamma, pu, pk, n, stream))
 
 
 # ---- solver ---------------------------------------------------------------------------

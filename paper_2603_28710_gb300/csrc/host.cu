@@ -436,6 +436,19 @@ adg_status after_state_set(adg_solver* s) {
 
 }  // namespace
 
+namespace adg {
+// Helpers for adg_rhs_noalloc (noalloc.cu): the same operator tables without a handle,
+// and the per-thread error text that adg_last_error(NULL) returns.
+void noalloc_build_tables(int N, const double* h, OpTables* T) {
+  adg_solver tmp;
+  tmp.N = N;
+  for (int d = 0; d < 3; ++d) tmp.h[d] = h[d];
+  build_tables(&tmp);
+  *T = tmp.tab;
+}
+void noalloc_set_error(const char* msg) { g_err = msg; }
+}  // namespace adg
+
 extern "C" {
 
 adg_status adg_default_options(adg_options* opt) {
