@@ -47,11 +47,14 @@ struct VolArgs {
   int stage, last; // stage index; last = 1 on the final stage of a step
   double ca, cb;   // 2R: dt*a_m, dt*b_m ; 2N: A_m, B_m
   double dt;
-  const double* in;  // stage input state (w, or r for 2R stages > 0)
-  double* w;         // solution (read + write)
-  double* x;         // 2R: r (write); 2N: q (read+write); RHS: k output
-  const void* fl;    // face fluxes [d][v][e][j] (storage type of the arithmetic)
-  void* tr;          // traces of the next stage input [d][side][v][e][j]
+  float2 caf, cbf, dtf;  // the same coefficients as FP32 pairs
+  const double* w_in;    // FP64 stage input when it is the solution (2N, and 2R stage 0)
+  const void* r_in;      // 2R stages > 0: the stage register r (operator storage type)
+  double* w;             // solution (read + write, FP64)
+  void* x;               // 2R: r (written); 2N: q (read + written); operator storage type
+  double* kout;          // RHS mode: k = M^-1 L(w_in), FP64
+  const void* fl;        // face fluxes [d][v][e][j] (storage type of the arithmetic)
+  void* tr;              // traces of the next stage input [d][side][v][e][j]
   int write_traces;
 };
 

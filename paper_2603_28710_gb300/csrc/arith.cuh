@@ -8,6 +8,32 @@
 
 namespace adg {
 
+// ---- conversions without F2F --------------------------------------------------------
+// On GB300 the F2F conversions between FP64 and FP32 issue at the FP64 rate (about 2 per
+// clock per SM, like DADD), 60x slower than FP32 arithmetic, so the reduced-precision
+// kernels convert with integer operations instead.  Valid for normal values with
+// |x| < 3.4e38; magnitudes below 2^-126 become signed zero.
+
+// double -> float, rounded to nearest (ties away from zero)
+__device__ __forceinline__ float d2f_int(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned sgn = (unsigned)(b >> 32) & 0x80000000u;
+  const unsigned long long r = (b & 0x7FFFFFFFFFFFFFFFull) + (1ull << 28);  // + half FP32 ulp
+  const int er = (int)(r >> 52);
+  const unsigned fb = sgn | ((unsigned)(er - 896) << 23) | ((unsigned)(r >> 29) & 0x7FFFFFu);
+  return __uint_as_float(er > 896 ? fb : sgn);
+}
+
+// float -> double, exact (subnormal floats give signed zero)
+__device__ __forceinline__ double f2d_int(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xFFu;
+  const unsigned long long sgn = (unsigned long long)(u & 0x80000000u) << 32;
+  const unsigned long long b =
+      sgn | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)(e ? b : sgn));
+}
+
 template <typename R>
 struct Arith;
 
@@ -29,8 +55,8 @@ struct Arith<float> {
   using Acc = float;
   __device__ static __forceinline__ float load(const float* p) { return __ldg(p); }
   __device__ static __forceinline__ void store(float* p, float v) { *p = v; }
-  __device__ static __forceinline__ double to_double(float v) { return (double)v; }
-  __device__ static __forceinline__ float from_double(double v) { return __double2float_rn(v); }
+  __device__ static __forceinline__ double to_double(float v) { return f2d_int(v); }
+  __device__ static __forceinline__ float from_double(double v) { return d2f_int(v); }
   __device__ static __forceinline__ float tab(const double*, const float2* f, int i) { return f[i].x; }
   __device__ static __forceinline__ float pair(double, float2 f) { return f.x; }
 };
@@ -44,8 +70,8 @@ struct Arith<df64> {
     return df64(v.x, v.y);
   }
   __device__ static __forceinline__ void store(float2* p, df64 v) { *p = make_float2(v.hi, v.lo); }
-  __device__ static __forceinline__ double to_double(df64 v) { return (double)v.hi + (double)v.lo; }
-  __device__ static __forceinline__ df64 from_double(double v) { return df64(v); }
+  __device__ static __forceinline__ double to_double(df64 v) { return f2d_int(v.hi) + f2d_int(v.lo); }
+  __device__ static __forceinline__ df64 from_double(double v) { return d2df_int(v); }
   __device__ static __forceinline__ df64 tab(const double*, const float2* f, int i) {
     return df64(f[i].x, f[i].y);
   }

@@ -27,12 +27,28 @@ struct df64 {
   float hi, lo;
   __device__ __forceinline__ df64() {}
   __device__ __forceinline__ df64(float h, float l) : hi(h), lo(l) {}
-  // exact split of an FP64 value into hi + lo (lo rounded: total error <= 2^-48 |x|)
-  __device__ __forceinline__ explicit df64(double x) {
-    hi = __double2float_rn(x);
-    lo = __double2float_rn(x - (double)hi);
-  }
+  __device__ __forceinline__ explicit df64(float h) : hi(h), lo(0.0f) {}
 };
+
+// Split of an FP64 value into an FP32 pair with integer operations only (see arith.cuh on
+// the cost of F2F): hi = x rounded to 24 significant bits, lo = x - hi (|lo| <= ulp(hi)/2,
+// the residual's integer mantissa is rounded to 24 bits, total error <= 2^-49 |x|).
+// lo needs |x| >= 2^-74 (else it is dropped: FP32 accuracy for tiny values); |x| < 2^-126
+// gives (0, 0).
+__device__ __forceinline__ df64 d2df_int(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned sgn = (unsigned)(b >> 32) & 0x80000000u;
+  const unsigned long long a = b & 0x7FFFFFFFFFFFFFFFull;
+  const unsigned long long hb = (a + (1ull << 28)) & ~((1ull << 29) - 1ull);
+  const int e = (int)(a >> 52);
+  const int eh = (int)(hb >> 52);
+  const float hi = __uint_as_float(sgn | ((unsigned)(eh - 896) << 23) | ((unsigned)(hb >> 29) & 0x7FFFFFu));
+  const long long dres = (long long)(a - hb);  // (|x| - |hi|) in units of 2^(e-1075), |dres| <= 2^28
+  const float scale = __uint_as_float((unsigned)(e - 948) << 23);  // 2^(e-1075)
+  float lo = (e >= 949) ? __int2float_rn((int)dres) * scale : 0.0f;
+  lo = __uint_as_float(__float_as_uint(lo) ^ sgn);
+  return (eh > 896) ? df64(hi, lo) : df64(__uint_as_float(sgn), 0.0f);
+}
 
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = __fadd_rn(a, b);

@@ -33,7 +33,7 @@ struct adg_solver {
   bool own_stream = false;
   // device memory
   double* w = nullptr;
-  double* x = nullptr;       // 2R: r ; 2N: q
+  void* x = nullptr;         // 2R: r ; 2N: q (operator storage type)
   void* tr = nullptr;        // traces
   void* fl = nullptr;        // face fluxes
   void* ring = nullptr;      // delayed-flux history
@@ -499,11 +499,18 @@ adg_status adg_create(const adg_mesh* mesh, int degree, const int P[3], int max_
   }
   int64_t ne = 1;
   for (int d = 0; d < mesh->dim; ++d) {
-    if (mesh->n_elem[d] < 1) return fail(nullptr, ADG_ERR_INVALID, "n_elem must be >= 1");
+    if (mesh->n_elem[d] < 1 || mesh->n_elem[d] > (1 << 20))
+      return fail(nullptr, ADG_ERR_INVALID, "n_elem must be in 1..2^20");
     if (P[d] < 1 || mesh->n_elem[d] % P[d] != 0)
       return fail(nullptr, ADG_ERR_INVALID, "P[d] must divide n_elem[d]");
     if (!(mesh->hi[d] > mesh->lo[d])) return fail(nullptr, ADG_ERR_INVALID, "hi must exceed lo");
     ne *= mesh->n_elem[d];
+  }
+  {
+    const int64_t nd = mesh->dim == 3 ? (int64_t)(degree + 1) * (degree + 1) * (degree + 1)
+                                      : (int64_t)(degree + 1) * (degree + 1);
+    if ((int64_t)(mesh->dim + 2) * ne * nd >= ((int64_t)1 << 31))
+      return fail(nullptr, ADG_ERR_UNSUPPORTED, "meshes with 2^31 or more degrees of freedom are not supported");
   }
   if (!kernels_available((int)o.precision, mesh->dim, degree + 1))
     return fail(nullptr, ADG_ERR_UNSUPPORTED, "no kernels built for this precision/degree");
@@ -591,7 +598,7 @@ adg_status adg_create(const adg_mesh* mesh, int degree, const int P[3], int max_
   const size_t nfl = (size_t)s->dim * s->NV * ne * s->NF;
   s->red_blocks = 152 * 4;
   alloc((void**)&s->w, nst * sizeof(double));
-  alloc((void**)&s->x, nst * sizeof(double));
+  alloc(&s->x, nst * sb);
   alloc(&s->tr, ntr * sb);
   alloc(&s->fl, nfl * sb);
   alloc((void**)&s->tab_dev, sizeof(OpTables));
@@ -720,12 +727,15 @@ adg_status adg_step(adg_solver* s, int n_steps) {
       if (s->rk2n) {
         va.ca = s->rka[m];
         va.cb = s->rkb[m];
-        va.in = s->w;
       } else {
         va.ca = s->dt * s->rka[m];
         va.cb = s->dt * s->rkb[m];
-        va.in = (m == 0) ? s->w : s->x;
       }
+      va.caf = split2(va.ca);
+      va.cbf = split2(va.cb);
+      va.dtf = split2(va.dt);
+      va.w_in = s->w;
+      va.r_in = s->x;
       va.w = s->w;
       va.x = s->x;
       va.fl = s->fl;
@@ -777,8 +787,8 @@ adg_status adg_rhs(adg_solver* s, const double* u, double* k, int64_t count, int
   va.gamma = s->opt.gamma;
   va.gammaf = split2(s->opt.gamma);
   va.mode = kModeRHS;
-  va.in = ud;
-  va.x = kd;
+  va.w_in = ud;
+  va.kout = kd;
   va.fl = s->fl;
   va.tr = s->tr;
   va.write_traces = 0;

@@ -1,7 +1,7 @@
 // Kernel templates of the ADG right-hand side, parameterised by dimension D, nodes per
 // direction N = degree + 1 and the arithmetic type R of the operator (double, float or
-// the FP32-pair type of df64.cuh).  The solution and the Runge-Kutta registers are FP64
-// in every variant.
+// the FP32-pair type of df64.cuh).  The solution w is FP64 in every variant; the RK
+// register (r or q) is stored in the operator's storage type.
 //
 // Per Runge-Kutta stage the solver runs two kernels:
 //   flux_kernel : one thread per (direction, face, face node): numerical flux of Eq. 8-9
@@ -12,6 +12,7 @@
 //                 inverse mass (diagonal for collocated Gauss points; folded into the
 //                 tables), the low-storage RK update (Eq. 10 or the 2N form), and the
 //                 face traces of the next stage input.
+// Index arithmetic is 32-bit: the host rejects meshes with 2^31 or more degrees of freedom.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -36,28 +37,25 @@ struct Tile {
   static constexpr int THREADS = EPB * ND;
 };
 
-__device__ __forceinline__ void elem_coords(const MeshArgs& m, int64_t e, int* c) {
-  int64_t t = e;
-  c[0] = (int)(t % m.n[0]);
-  t /= m.n[0];
-  c[1] = (int)(t % m.n[1]);
-  t /= m.n[1];
-  c[2] = (int)t;
+__device__ __forceinline__ void elem_coords(const MeshArgs& m, int e, int* c) {
+  const int q = e / m.n[0];
+  c[0] = e - q * m.n[0];
+  c[2] = q / m.n[1];
+  c[1] = q - c[2] * m.n[1];
 }
 
 // index of the neighbour of element e (coordinates c) one step s (+1/-1) along d, periodic
-__device__ __forceinline__ int64_t elem_shift(const MeshArgs& m, int64_t e, const int* c, int d,
-                                              int s) {
+__device__ __forceinline__ int elem_shift(const MeshArgs& m, int e, const int* c, int d, int s) {
   int k = c[d] + s;
   if (k < 0) k += m.n[d];
   if (k >= m.n[d]) k -= m.n[d];
-  return e + (int64_t)(k - c[d]) * m.es[d];
+  return e + (k - c[d]) * (int)m.es[d];
 }
 
 // Pointwise Euler flux columns F_d(w), d < D (Eq. 2-3, no source).
 template <int D, typename R>
-__device__ __forceinline__ void euler_flux_all(const R* w, R gm1, R (*F)[D + 2]) {
-  R irho = r_rcp(w[0]);
+__device__ __forceinline__ void euler_flux_all(const R (&w)[D + 2], R gm1, R (&F)[D][D + 2]) {
+  const R irho = r_rcp(w[0]);
   R u[D];
   R kin2 = R(0.0f);
 #pragma unroll
@@ -65,8 +63,8 @@ __device__ __forceinline__ void euler_flux_all(const R* w, R gm1, R (*F)[D + 2])
     u[d] = w[1 + d] * irho;
     kin2 = r_fma(w[1 + d], u[d], kin2);
   }
-  R p = gm1 * (w[D + 1] - R(0.5f) * kin2);
-  R ep = w[D + 1] + p;
+  const R p = gm1 * (w[D + 1] - R(0.5f) * kin2);
+  const R ep = w[D + 1] + p;
 #pragma unroll
   for (int d = 0; d < D; ++d) {
     F[d][0] = w[1 + d];
@@ -77,38 +75,47 @@ __device__ __forceinline__ void euler_flux_all(const R* w, R gm1, R (*F)[D + 2])
   }
 }
 
+// Flux column along e_d and |u|^2 + c^2 of one trace state (d is a runtime direction;
+// selects instead of indexing keep everything in registers).
+template <int D, typename R>
+__device__ __forceinline__ void side_flux(const R (&w)[D + 2], int d, R gamma, R gm1,
+                                          R (&fd)[D + 2], R& s2) {
+  const R irho = r_rcp(w[0]);
+  R u2 = R(0.0f), kin2 = R(0.0f), ud = R(0.0f), md = w[1];
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    const R uc = w[1 + c] * irho;
+    u2 = r_fma(uc, uc, u2);
+    kin2 = r_fma(w[1 + c], uc, kin2);
+    if (c == d) {
+      ud = uc;
+      md = w[1 + c];
+    }
+  }
+  const R p = gm1 * (w[D + 1] - R(0.5f) * kin2);
+  s2 = u2 + gamma * p * irho;
+  fd[0] = md;
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    fd[1 + c] = w[1 + c] * ud;
+    if (c == d) fd[1 + c] = fd[1 + c] + p;
+  }
+  fd[D + 1] = (w[D + 1] + p) * ud;
+}
+
 // Rusanov flux along +e_d (Eq. 8) with lambda = 1/2 max(sqrt(|u|^2 + c^2)) (Eq. 9).
 template <int D, typename R>
-__device__ __forceinline__ void llf_flux(const R* wm, const R* wp, int d, R gamma, R* f) {
+__device__ __forceinline__ void llf_flux(const R (&wm)[D + 2], const R (&wp)[D + 2], int d,
+                                         R gamma, R (&f)[D + 2]) {
   constexpr int NV = D + 2;
-  R gm1 = gamma - R(1.0f);
-  R s2[2];
-  R fd[2][NV];
-  const R* ws[2] = {wm, wp};
+  const R gm1 = gamma - R(1.0f);
+  R fm[NV], fp[NV], sm, sp;
+  side_flux<D, R>(wm, d, gamma, gm1, fm, sm);
+  side_flux<D, R>(wp, d, gamma, gm1, fp, sp);
+  const R lam = R(0.5f) * r_sqrt(r_max(sm, sp));
+  const R hl = R(0.5f) * lam;
 #pragma unroll
-  for (int side = 0; side < 2; ++side) {
-    const R* w = ws[side];
-    R irho = r_rcp(w[0]);
-    R u2 = R(0.0f), kin2 = R(0.0f), ud = R(0.0f);
-#pragma unroll
-    for (int c = 0; c < D; ++c) {
-      R uc = w[1 + c] * irho;
-      u2 = r_fma(uc, uc, u2);
-      kin2 = r_fma(w[1 + c], uc, kin2);
-      if (c == d) ud = uc;
-    }
-    R p = gm1 * (w[D + 1] - R(0.5f) * kin2);
-    s2[side] = u2 + gamma * p * irho;
-    fd[side][0] = w[1 + d];
-#pragma unroll
-    for (int c = 0; c < D; ++c) fd[side][1 + c] = w[1 + c] * ud;
-    fd[side][1 + d] = fd[side][1 + d] + p;
-    fd[side][D + 1] = (w[D + 1] + p) * ud;
-  }
-  R lam = R(0.5f) * r_sqrt(r_max(s2[0], s2[1]));
-  R hl = R(0.5f) * lam;
-#pragma unroll
-  for (int v = 0; v < NV; ++v) f[v] = R(0.5f) * (fd[0][v] + fd[1][v]) + hl * (wm[v] - wp[v]);
+  for (int v = 0; v < NV; ++v) f[v] = R(0.5f) * (fm[v] + fp[v]) + hl * (wm[v] - wp[v]);
 }
 
 // Transverse coordinates of face node j of a face normal to d -> base node index of the
@@ -144,28 +151,28 @@ __device__ __forceinline__ int face_index(int d, const int* ix) {
 // Traces of a tile of elements held in shared memory sX[el][v][node] -> tr.
 template <int D, int N, typename R>
 __device__ __forceinline__ void write_traces(const MeshArgs& m, const OpTables* tab, const R* sX,
-                                             int64_t e0, typename Arith<R>::S* tr) {
+                                             int e0, typename Arith<R>::S* tr) {
   using T = Tile<D, N>;
   constexpr int ND = T::ND, NF = T::NF, NV = T::NV, EPB = T::EPB;
   constexpr int TOTAL = EPB * 2 * D * NV * NF;
+  const int ne = (int)m.ne;
   for (int g = threadIdx.x; g < TOTAL; g += blockDim.x) {
-    int jj = g % (EPB * NF);
-    int rest = g / (EPB * NF);  // (d*2 + side)*NV + v
-    int el = jj / NF, j = jj - el * NF;
-    int64_t e = e0 + el;
-    if (e >= m.ne) continue;
-    int v = rest % NV, ds = rest / NV;
-    int d = ds >> 1, side = ds & 1;
-    int base = line_base<D, N>(d, j);
-    int stride = 1;
-    for (int c = 0; c < d; ++c) stride *= N;
+    const int jj = g % (EPB * NF);
+    const int rest = g / (EPB * NF);  // (d*2 + side)*NV + v
+    const int el = jj / NF, j = jj - el * NF;
+    const int e = e0 + el;
+    if (e >= ne) continue;
+    const int v = rest % NV, ds = rest / NV;
+    const int d = ds >> 1, side = ds & 1;
+    const int base = line_base<D, N>(d, j);
+    const int stride = d == 0 ? 1 : (d == 1 ? N : N * N);
     const double* tw = side ? tab->Tp : tab->Tm;
     const float2* twf = side ? tab->Tpf : tab->Tmf;
     typename Arith<R>::Acc acc = acc_zero(typename Arith<R>::Acc());
 #pragma unroll
     for (int a = 0; a < N; ++a)
       acc = acc_fma(Arith<R>::tab(tw, twf, a), sX[(el * NV + v) * ND + base + a * stride], acc);
-    Arith<R>::store(tr + ((int64_t)(ds * NV + v) * m.ne + e) * NF + j, acc_result(acc));
+    Arith<R>::store(tr + ((ds * NV + v) * ne + e) * NF + j, acc_result(acc));
   }
 }
 
@@ -176,16 +183,83 @@ __global__ void __launch_bounds__(Tile<D, N>::THREADS) trace_kernel(const TraceA
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* sX = reinterpret_cast<R*>(smem_raw);
   const int el = threadIdx.x / ND, node = threadIdx.x - el * ND;
-  const int64_t e0 = (int64_t)blockIdx.x * EPB;
-  const int64_t e = e0 + el;
-  if (e < A.m.ne) {
+  const int e0 = blockIdx.x * EPB;
+  const int e = e0 + el;
+  const int ne = (int)A.m.ne;
+  if (e < ne) {
 #pragma unroll
     for (int v = 0; v < NV; ++v)
-      sX[(el * NV + v) * ND + node] = Arith<R>::from_double(A.u[((int64_t)v * A.m.ne + e) * ND + node]);
+      sX[(el * NV + v) * ND + node] = Arith<R>::from_double(A.u[(v * ne + e) * ND + node]);
   }
   __syncthreads();
   write_traces<D, N, R>(A.m, A.tab, sX, e0, reinterpret_cast<typename Arith<R>::S*>(A.tr));
 }
+
+// ---- Runge-Kutta update of one node -------------------------------------------------
+// Native FP64: everything in FP64.  FP32 / FP32 pair: the RK register and the stage input
+// stay in the operator arithmetic; only the accumulation into w is FP64 (one or two DADD).
+__device__ __forceinline__ double add_increment(double w0, double d) { return w0 + d; }
+__device__ __forceinline__ double add_increment(double w0, float d) { return w0 + f2d_int(d); }
+__device__ __forceinline__ double add_increment(double w0, df64 d) {
+  return (w0 + f2d_int(d.hi)) + f2d_int(d.lo);
+}
+
+template <typename R>
+struct Update {
+  using S = typename Arith<R>::S;
+  // returns the next stage input at this node/variable
+  __device__ static __forceinline__ R apply(const VolArgs& A, int idx, R k, R u_in) {
+    if (A.mode == kModeRHS) {
+      A.kout[idx] = Arith<R>::to_double(k);
+      return u_in;
+    }
+    const double w0 = A.w[idx];
+    S* x = reinterpret_cast<S*>(A.x);
+    if (A.mode == kMode2R) {
+      const R cb = Arith<R>::pair(A.cb, A.cbf), ca = Arith<R>::pair(A.ca, A.caf);
+      const double w1 = add_increment(w0, cb * k);
+      A.w[idx] = w1;
+      if (A.last) return Arith<R>::from_double(w1);
+      const R w0r = (A.stage == 0) ? u_in : Arith<R>::from_double(w0);
+      const R r1 = r_fma(ca, k, w0r);
+      Arith<R>::store(x + idx, r1);
+      return r1;
+    }
+    const R cA = Arith<R>::pair(A.ca, A.caf), cB = Arith<R>::pair(A.cb, A.cbf);
+    const R dt = Arith<R>::pair(A.dt, A.dtf);
+    const R q1 = (A.stage > 0) ? r_fma(cA, Arith<R>::load(x + idx), dt * k) : dt * k;
+    const double w1 = add_increment(w0, cB * q1);
+    A.w[idx] = w1;
+    if (!A.last) Arith<R>::store(x + idx, q1);
+    return Arith<R>::from_double(w1);
+  }
+};
+
+template <>
+struct Update<double> {
+  __device__ static __forceinline__ double apply(const VolArgs& A, int idx, double k, double u_in) {
+    if (A.mode == kModeRHS) {
+      A.kout[idx] = k;
+      return u_in;
+    }
+    const double w0 = A.w[idx];
+    double* x = reinterpret_cast<double*>(A.x);
+    if (A.mode == kMode2R) {
+      const double w1 = fma(A.cb, k, w0);
+      A.w[idx] = w1;
+      if (A.last) return w1;
+      const double r1 = fma(A.ca, k, w0);
+      x[idx] = r1;
+      return r1;
+    }
+    const double q0 = A.stage > 0 ? x[idx] : 0.0;
+    const double q1 = fma(A.ca, q0, A.dt * k);
+    const double w1 = fma(A.cb, q1, w0);
+    A.w[idx] = w1;
+    if (!A.last) x[idx] = q1;
+    return w1;
+  }
+};
 
 template <int D, int N, typename R>
 __global__ void __launch_bounds__(Tile<D, N>::THREADS) vol_kernel(const VolArgs A) {
@@ -195,10 +269,10 @@ __global__ void __launch_bounds__(Tile<D, N>::THREADS) vol_kernel(const VolArgs 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* sF = reinterpret_cast<R*>(smem_raw);  // [EPB][D][NV][ND]
   const int el = threadIdx.x / ND, node = threadIdx.x - el * ND;
-  const int64_t e0 = (int64_t)blockIdx.x * EPB;
-  const int64_t e = e0 + el;
-  const bool active = e < A.m.ne;
-  const int64_t ne = A.m.ne;
+  const int e0 = blockIdx.x * EPB;
+  const int ne = (int)A.m.ne;
+  const int e = e0 + el;
+  const bool active = e < ne;
 
   int ix[3] = {node % N, (node / N) % N, node / (N * N)};
   int ec[3] = {0, 0, 0};
@@ -206,9 +280,13 @@ __global__ void __launch_bounds__(Tile<D, N>::THREADS) vol_kernel(const VolArgs 
 
   // 1. stage input at this node and its pointwise fluxes
   R u[NV];
+  const bool from_r = (A.mode == kMode2R && A.stage > 0);
+  const S* rin = reinterpret_cast<const S*>(A.r_in);
 #pragma unroll
-  for (int v = 0; v < NV; ++v)
-    u[v] = active ? Arith<R>::from_double(A.in[((int64_t)v * ne + e) * ND + node]) : R(1.0f);
+  for (int v = 0; v < NV; ++v) {
+    const int idx = (v * ne + e) * ND + node;
+    u[v] = !active ? R(1.0f) : (from_r ? Arith<R>::load(rin + idx) : Arith<R>::from_double(A.w_in[idx]));
+  }
   {
     R F[D][NV];
     euler_flux_all<D, R>(u, Arith<R>::pair(A.gamma, A.gammaf) - R(1.0f), F);
@@ -226,9 +304,9 @@ __global__ void __launch_bounds__(Tile<D, N>::THREADS) vol_kernel(const VolArgs 
   for (int v = 0; v < NV; ++v) acc[v] = acc_zero(Acc());
   const S* fl = reinterpret_cast<const S*>(A.fl);
   if (active) {
-    int stride = 1;
 #pragma unroll
     for (int d = 0; d < D; ++d) {
+      const int stride = d == 0 ? 1 : (d == 1 ? N : N * N);
       const int base = node - ix[d] * stride;
 #pragma unroll
       for (int a = 0; a < N; ++a) {
@@ -237,55 +315,29 @@ __global__ void __launch_bounds__(Tile<D, N>::THREADS) vol_kernel(const VolArgs 
         for (int v = 0; v < NV; ++v)
           acc[v] = acc_fma(q, sF[((el * D + d) * NV + v) * ND + base + a * stride], acc[v]);
       }
-      stride *= N;
     }
 #pragma unroll
     for (int d = 0; d < D; ++d) {
       const int j = face_index<D, N>(d, ix);
-      const int64_t elo = elem_shift(A.m, e, ec, d, -1);
+      const int elo = elem_shift(A.m, e, ec, d, -1);
       const R lp = Arith<R>::tab(A.tab->Lp[d], A.tab->Lpf[d], ix[d]);
       const R lm = Arith<R>::tab(A.tab->Lm[d], A.tab->Lmf[d], ix[d]);
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        R fhi = Arith<R>::load(fl + ((int64_t)(d * NV + v) * ne + e) * NF + j);
-        R flo = Arith<R>::load(fl + ((int64_t)(d * NV + v) * ne + elo) * NF + j);
+        const R fhi = Arith<R>::load(fl + ((d * NV + v) * ne + e) * NF + j);
+        const R flo = Arith<R>::load(fl + ((d * NV + v) * ne + elo) * NF + j);
         acc[v] = acc_fma(lm, flo, acc[v]);
         acc[v] = acc_fma(-lp, fhi, acc[v]);
       }
     }
   }
 
-  // 3. Runge-Kutta update in FP64; xnext = input of the next stage
+  // 3. Runge-Kutta update; xnext = input of the next stage
   R xnext[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
-    const int64_t idx = ((int64_t)v * ne + e) * ND + node;
-    double k = Arith<R>::to_double(acc_result(acc[v]));
-    double xn = 0.0;
-    if (active) {
-      if (A.mode == kModeRHS) {
-        A.x[idx] = k;
-      } else if (A.mode == kMode2R) {
-        double w0 = A.w[idx];
-        double w1 = fma(A.cb, k, w0);
-        A.w[idx] = w1;
-        if (!A.last) {
-          xn = fma(A.ca, k, w0);
-          A.x[idx] = xn;
-        } else {
-          xn = w1;
-        }
-      } else {
-        double w0 = A.w[idx];
-        double q0 = A.stage > 0 ? A.x[idx] : 0.0;
-        double q1 = fma(A.ca, q0, A.dt * k);
-        double w1 = fma(A.cb, q1, w0);
-        A.w[idx] = w1;
-        if (!A.last) A.x[idx] = q1;
-        xn = w1;
-      }
-    }
-    xnext[v] = Arith<R>::from_double(xn);
+    const int idx = (v * ne + e) * ND + node;
+    xnext[v] = active ? Update<R>::apply(A, idx, acc_result(acc[v]), u[v]) : R(0.0f);
   }
 
   // 4. traces of the next stage input
@@ -307,85 +359,78 @@ __device__ __forceinline__ uint64_t splitmix64_dev(uint64_t x) {
   return z ^ (z >> 31);
 }
 
+// grid: x over (element, face node) of one direction, y = direction d
 template <int D, int N, typename R>
 __global__ void __launch_bounds__(256) flux_kernel(const FluxArgs A) {
   using S = typename Arith<R>::S;
   constexpr int NF = IPow<N, D - 1>::value, NV = D + 2;
-  const int64_t ne = A.m.ne;
-  const int64_t per_dir = ne * NF;
-  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= D * per_dir) return;
-  const int d = (int)(g / per_dir);
-  const int64_t rem = g - d * per_dir;
-  const int64_t e = rem / NF;
-  const int j = (int)(rem - e * NF);
+  const int ne = (int)A.m.ne;
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= ne * NF) return;
+  const int d = blockIdx.y;
+  const int e = g / NF;
+  const int j = g - e * NF;
   int ec[3];
   elem_coords(A.m, e, ec);
-  const int64_t ehi = elem_shift(A.m, e, ec, d, +1);
+  const int ehi = elem_shift(A.m, e, ec, d, +1);
   const S* tr = reinterpret_cast<const S*>(A.tr);
   R wm[NV], wp[NV], f[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
-    wm[v] = Arith<R>::load(tr + ((int64_t)((d * 2 + 1) * NV + v) * ne + e) * NF + j);
-    wp[v] = Arith<R>::load(tr + ((int64_t)((d * 2 + 0) * NV + v) * ne + ehi) * NF + j);
+    wm[v] = Arith<R>::load(tr + (((d * 2 + 1) * NV + v) * ne + e) * NF + j);
+    wp[v] = Arith<R>::load(tr + (((d * 2 + 0) * NV + v) * ne + ehi) * NF + j);
   }
   const R gamma = Arith<R>::pair(A.gamma, A.gammaf);
-  const int slot = A.pe_mode ? A.pe_slot[(int64_t)d * ne + e] : -1;
+  const int slot = A.pe_mode ? A.pe_slot[d * ne + e] : -1;
   if (slot < 0) {
     llf_flux<D, R>(wm, wp, d, gamma, f);
   } else {
     S* ring = reinterpret_cast<S*>(A.ring);
     const bool traces = (A.flux_kind == 3);
-    const int64_t lvl_stride = (int64_t)(traces ? 2 : 1) * NV * A.npe * NF;
+    const int npe = (int)A.npe;
+    const int lvl_stride = (traces ? 2 : 1) * NV * npe * NF;
     int kt = A.uniform_delay;
     if (A.random) {
       const int iface = A.pe_iface[slot];
-      uint64_t ctr = (uint64_t)A.step * (uint64_t)A.n_iface + (uint64_t)iface;
+      const uint64_t ctr = (uint64_t)A.step * (uint64_t)A.n_iface + (uint64_t)iface;
       kt = (int)(splitmix64_dev(A.seed ^ ctr) % (uint64_t)(A.dmax + 1));
       const int64_t need = (A.nterms == 1) ? kt : kt + A.np;
       if (A.step - need < 0) kt = 0;
     }
-    if (A.store) {
-      S* dst = ring + (int64_t)A.head * lvl_stride;
+    if (A.store && traces) {
+      S* dst = ring + A.head * lvl_stride;
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        if (traces) {
-          Arith<R>::store(dst + ((int64_t)(0 * NV + v) * A.npe + slot) * NF + j, wm[v]);
-          Arith<R>::store(dst + ((int64_t)(1 * NV + v) * A.npe + slot) * NF + j, wp[v]);
-        }
+        Arith<R>::store(dst + (v * npe + slot) * NF + j, wm[v]);
+        Arith<R>::store(dst + ((NV + v) * npe + slot) * NF + j, wp[v]);
       }
     }
-    if (kt == 0) {
-      llf_flux<D, R>(wm, wp, d, gamma, f);
+    if (kt == 0 || (A.store && !traces)) {
+      R fr[NV];
+      llf_flux<D, R>(wm, wp, d, gamma, fr);
       if (A.store && !traces) {
-        S* dst = ring + (int64_t)A.head * lvl_stride;
+        S* dst = ring + A.head * lvl_stride;
 #pragma unroll
-        for (int v = 0; v < NV; ++v) Arith<R>::store(dst + ((int64_t)v * A.npe + slot) * NF + j, f[v]);
+        for (int v = 0; v < NV; ++v) Arith<R>::store(dst + (v * npe + slot) * NF + j, fr[v]);
       }
-    } else {
-      if (A.store && !traces) {
-        R fr[NV];
-        llf_flux<D, R>(wm, wp, d, gamma, fr);
-        S* dst = ring + (int64_t)A.head * lvl_stride;
 #pragma unroll
-        for (int v = 0; v < NV; ++v) Arith<R>::store(dst + ((int64_t)v * A.npe + slot) * NF + j, fr[v]);
-      }
+      for (int v = 0; v < NV; ++v) f[v] = fr[v];
+    }
+    if (kt != 0) {
       const int off = A.random ? kt : 0;
       using Acc = typename Arith<R>::Acc;
       Acc am[NV], ap[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) { am[v] = acc_zero(Acc()); ap[v] = acc_zero(Acc()); }
       for (int l = 0; l < A.nterms; ++l) {
-        int lvl = A.head - off - l;
-        lvl %= A.depth;
+        int lvl = (A.head - off - l) % A.depth;
         if (lvl < 0) lvl += A.depth;
         const R c = Arith<R>::pair(A.ctab[kt][l], A.ctabf[kt][l]);
-        const S* src = ring + (int64_t)lvl * lvl_stride;
+        const S* src = ring + lvl * lvl_stride;
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          am[v] = acc_fma(c, Arith<R>::load(src + ((int64_t)v * A.npe + slot) * NF + j), am[v]);
-          if (traces)
-            ap[v] = acc_fma(c, Arith<R>::load(src + ((int64_t)(NV + v) * A.npe + slot) * NF + j), ap[v]);
+          am[v] = acc_fma(c, Arith<R>::load(src + (v * npe + slot) * NF + j), am[v]);
+          if (traces) ap[v] = acc_fma(c, Arith<R>::load(src + ((NV + v) * npe + slot) * NF + j), ap[v]);
         }
       }
       if (traces) {
@@ -401,7 +446,7 @@ __global__ void __launch_bounds__(256) flux_kernel(const FluxArgs A) {
   }
   S* fl = reinterpret_cast<S*>(A.fl);
 #pragma unroll
-  for (int v = 0; v < NV; ++v) Arith<R>::store(fl + ((int64_t)(d * NV + v) * ne + e) * NF + j, f[v]);
+  for (int v = 0; v < NV; ++v) Arith<R>::store(fl + ((d * NV + v) * ne + e) * NF + j, f[v]);
 }
 
 // ------------------------------------------------------------------------------------
@@ -410,8 +455,8 @@ __global__ void __launch_bounds__(256) flux_kernel(const FluxArgs A) {
 template <int D, int N, typename R>
 cudaError_t launch_trace_t(const TraceArgs& a, cudaStream_t s) {
   using T = Tile<D, N>;
-  int64_t blocks = (a.m.ne + T::EPB - 1) / T::EPB;
-  size_t smem = sizeof(R) * T::EPB * T::NV * T::ND;
+  const int64_t blocks = (a.m.ne + T::EPB - 1) / T::EPB;
+  const size_t smem = sizeof(R) * T::EPB * T::NV * T::ND;
   trace_kernel<D, N, R><<<(unsigned)blocks, T::THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }
@@ -419,8 +464,8 @@ cudaError_t launch_trace_t(const TraceArgs& a, cudaStream_t s) {
 template <int D, int N, typename R>
 cudaError_t launch_vol_t(const VolArgs& a, cudaStream_t s) {
   using T = Tile<D, N>;
-  int64_t blocks = (a.m.ne + T::EPB - 1) / T::EPB;
-  size_t smem = sizeof(R) * T::EPB * D * T::NV * T::ND;
+  const int64_t blocks = (a.m.ne + T::EPB - 1) / T::EPB;
+  const size_t smem = sizeof(R) * T::EPB * D * T::NV * T::ND;
   if (smem > 48 * 1024) {
     cudaError_t err = cudaFuncSetAttribute(vol_kernel<D, N, R>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -433,18 +478,15 @@ cudaError_t launch_vol_t(const VolArgs& a, cudaStream_t s) {
 template <int D, int N, typename R>
 cudaError_t launch_flux_t(const FluxArgs& a, cudaStream_t s) {
   constexpr int NF = IPow<N, D - 1>::value;
-  int64_t total = (int64_t)D * a.m.ne * NF;
-  int64_t blocks = (total + 255) / 256;
-  flux_kernel<D, N, R><<<(unsigned)blocks, 256, 0, s>>>(a);
+  const int64_t per_dir = a.m.ne * NF;
+  dim3 grid((unsigned)((per_dir + 255) / 256), D);
+  flux_kernel<D, N, R><<<grid, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 
 // Dispatch over (dim, N) for one arithmetic R.
 template <typename R>
 struct Dispatch {
-  template <int D, int N>
-  static cudaError_t trace(const TraceArgs& a, cudaStream_t s) { return launch_trace_t<D, N, R>(a, s); }
-
   static cudaError_t run_trace(int dim, int N, const TraceArgs& a, cudaStream_t s);
   static cudaError_t run_flux(int dim, int N, const FluxArgs& a, cudaStream_t s);
   static cudaError_t run_vol(int dim, int N, const VolArgs& a, cudaStream_t s);

@@ -132,8 +132,8 @@ extern "C" adg_status adg_rhs_noalloc(const adg_mesh* mesh, int degree, double g
   va.tab = tab_dev;
   va.gamma = gamma;
   va.mode = kModeRHS;
-  va.in = u;
-  va.x = k;
+  va.w_in = u;
+  va.kout = k;
   va.fl = fl;
   va.tr = tr;
   va.write_traces = 0;
