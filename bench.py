@@ -162,9 +162,8 @@ class ClockSampler:
 
 
 # ---- oracle CPU baseline ---------------------------------------------------------------
-def oracle_sample(time_steps):
-    """Times the CPU oracle on the full-size workload for a few time steps; returns
-    (GDoF-RK-stages/s, seconds)."""
+def make_oracle():
+    """The CPU oracle on the full-size workload with the CFL-0.1 time step."""
     import oracle
     o = oracle.Oracle(n_elem=(N_ELEM, N_ELEM), degree=DEGREE, P=(P, P), max_delay=L, flux="at",
                       rk="ck45", dt=1.0)
@@ -173,6 +172,13 @@ def oracle_sample(time_steps):
     o = oracle.Oracle(n_elem=(N_ELEM, N_ELEM), degree=DEGREE, P=(P, P), max_delay=L, flux="at",
                       rk="ck45", dt=dt)
     o.set_state(u0)
+    return o
+
+
+def oracle_sample(time_steps):
+    """Times the CPU oracle on the full-size workload for a few time steps; returns
+    (GDoF-RK-stages/s, seconds)."""
+    o = make_oracle()
     t0 = time.perf_counter()
     o.step(time_steps)
     sec = time.perf_counter() - t0
@@ -181,14 +187,17 @@ def oracle_sample(time_steps):
 
 
 def run_reference(args, rank, world):
+    """The oracle as the reference arm: one RK time step of the full workload per step,
+    single-threaded, on the host cores (rank 0 only)."""
     if rank != 0:
         return
+    o = make_oracle()
+    o.step(args.warmup)
     per = []
-    for _ in range(args.warmup):
-        oracle_sample(1)
     for _ in range(args.steps):
-        v, sec = oracle_sample(1)
-        per.append(sec)
+        t0 = time.perf_counter()
+        o.step(1)
+        per.append(time.perf_counter() - t0)
     total = sum(per)
     ndof = 4 * N_ELEM * N_ELEM * (DEGREE + 1) ** 2
     value = ndof * 5 * args.steps / total / 1e9
@@ -201,6 +210,50 @@ def run_reference(args, rank, world):
                                        "workload per step, single-threaded C oracle"},
             "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ---- multi-rank aggregation ---------------------------------------------------------------
+def reduce_max(x, device=None):
+    """Maximum of a float over all ranks (identity without an initialised process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(work_per_rank_per_step, steps, seconds_max, world):
+    """Whole-job throughput in G-units/s: every rank's work over the slowest rank's time."""
+    return world * work_per_rank_per_step * steps / seconds_max / 1e9
+
+
+def variant_run(adg, stream, precision, steps_per, k, warm, dt):
+    """Throughput and L2 error vs the exact vortex of one operator arithmetic on the bench
+    workload (fixed dt, same initial state)."""
+    import torch
+    s = adg.Solver(n_elem=(N_ELEM, N_ELEM), degree=DEGREE, P=(P, P), max_delay=L, flux="at",
+                   rk="ck45", dt=dt, precision=precision, stream=stream.cuda_stream)
+    s.init_vortex()
+    s.step(steps_per * warm)
+    torch.cuda.synchronize()
+    s.set_profiling(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step(steps_per * k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prof = s.get_profile()
+    ms = e0.elapsed_time(e1)
+    ndof = 4 * N_ELEM * N_ELEM * (DEGREE + 1) ** 2
+    info = s.info()
+    err = s.l2_error_vortex(info["t"])
+    s.close()
+    return {"value": ndof * 5 * steps_per * k / (ms * 1e-3) / 1e9,
+            "vol_ms_per_launch": prof["vol"][0] / max(prof["vol"][1], 1),
+            "flux_ms_per_launch": prof["flux"][0] / max(prof["flux"][1], 1),
+            "l2_error_vs_exact": [float(x) for x in err], "t": info["t"]}
 
 
 # ---- GPU arm -----------------------------------------------------------------------------
@@ -253,13 +306,8 @@ def run_gpu(args, rank, world, local_rank):
     prof = s.get_profile()
     s.set_profiling(False)
     ms_list = [a.elapsed_time(b) for a, b in ev]
-    ms = sum(ms_list)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * work * args.steps / (ms * 1e-3) / 1e9
+    ms = reduce_max(sum(ms_list), dev)
+    value = whole_job_value(work, args.steps, ms * 1e-3, world)
 
     # end to end through the public API: pinned host state in, 8 steps, state out
     host_in = torch.from_numpy(s.get_state()).pin_memory()
@@ -279,13 +327,8 @@ def run_gpu(args, rank, world, local_rank):
         s2.step(steps_per)
         s2.get_state(host_out)
     torch.cuda.synchronize()
-    e2e_sec = time.perf_counter() - t0
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_sec], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_sec = float(t.item())
-    e2e_value = world * work * args.steps / e2e_sec / 1e9
+    e2e_sec = reduce_max(time.perf_counter() - t0, dev)
+    e2e_value = whole_job_value(work, args.steps, e2e_sec, world)
     state_bytes = ndof * 8
 
     if rank != 0:
@@ -324,6 +367,17 @@ def run_gpu(args, rank, world, local_rank):
                "sample": f"{args.cpu_steps} RK time steps (5 stages each) of the full 256^2 p=4 "
                          f"workload, single-threaded C oracle, {sec:.1f} s"}
 
+    variants = None
+    if world == 1 and not args.no_variants:
+        variants = {}
+        for prec in ("fp64", "df64", "fp32"):
+            variants[prec] = variant_run(adg, stream, prec, steps_per, args.variant_steps, 2, dt)
+        base = variants["fp64"]
+        for prec, v in variants.items():
+            v["speedup_vs_fp64"] = v["value"] / base["value"]
+            v["l2_error_ratio_vs_fp64"] = [a / b for a, b in zip(v["l2_error_vs_exact"],
+                                                                 base["l2_error_vs_exact"])]
+
     clocks = clk.summary()
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -337,7 +391,8 @@ def run_gpu(args, rank, world, local_rank):
             "gpu_launches": int(vol_n + flux_n),
             "kernels": {"vol_kernel": {"ms_per_launch": vol_ms / max(vol_n, 1), "launches": vol_n},
                         "flux_kernel": {"ms_per_launch": flux_ms / max(flux_n, 1),
-                                        "launches": flux_n}}}
+                                        "launches": flux_n}},
+            "variants": variants}
     print(json.dumps(line), flush=True)
 
 
@@ -350,6 +405,9 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "df64"])
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the FP64 / FP32-pair / FP32 comparison runs")
+    ap.add_argument("--variant-steps", type=int, default=10)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

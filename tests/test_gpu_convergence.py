@@ -1,0 +1,79 @@
+"""The paper's accuracy study (Section 5.3, Figs. 6-7) on the GPU path.
+
+Isentropic vortex, 16x16 subdomains, maximum delay L = 4, t_final = 4.  DG(1)-LSERK2 and
+DG(2)-LSERK3 against their asynchronous forms with the standard flux and the AT flux.  The
+paper reports slopes N_p+1 for the synchronous and AT schemes and about 1 for the standard
+flux.  The paper does not give its time-step rule; with this library's rule
+(dt = cfl h / ((2p+1) max(|u|+c))) its CFL numbers 0.05 / 0.03 give time steps so short
+that on 32^2..256^2 the standard flux's delay error stays below the spatial error (all
+three schemes then converge at the spatial rate).  The test therefore runs at CFL 0.2 (the
+largest of 0.2 / 0.4 / 0.8 at which both delayed schemes are stable on the oracle) and
+extends the meshes until the O(dt) = O(h) delay error of the standard flux dominates.
+"""
+import numpy as np
+import pytest
+
+from paper_2603_28710_gb300 import adg
+
+pytestmark = pytest.mark.gpu
+
+MESHES = {1: (64, 128, 256, 512, 1024), 2: (32, 64, 128, 256, 512)}
+CFL = 0.2
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2603_28710_gb300 import build
+    build.build()
+
+
+def run(n, p, flux, cfl, precision="df64", T=4.0):
+    rk = {1: "rk22", 2: "rk33"}[p]
+    s = adg.Solver(n_elem=(n, n), degree=p, P=(16, 16), max_delay=4, flux=flux, rk=rk, cfl=cfl,
+                   t_end=T, precision=precision)
+    s.init_vortex()
+    nsteps = int(round(T / s.info()["dt"]))
+    s.step(nsteps)
+    assert s.check_finite()
+    e = s.l2_error_vortex(T)
+    s.close()
+    return e
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_convergence_orders_match_the_paper(p):
+    errs = {}
+    for flux in ("sync", "at", "std"):
+        errs[flux] = np.array([run(n, p, flux, CFL) for n in MESHES[p]])
+    for flux, e in errs.items():
+        slopes = np.log2(e[:-1] / e[1:])
+        print(f"p={p} {flux:5s} density/momentum/energy L2 errors:")
+        for n, row in zip(MESHES[p], e):
+            print(f"   {n:4d}^2  {row[0]:.3e} {row[1]:.3e} {row[2]:.3e}")
+        print(f"   slopes: {np.array2string(slopes, precision=2)}")
+    slope = lambda e: np.log2(e[:-1] / e[1:])
+    # synchronous and AT: order N_p + 1 on the finest pair of meshes
+    assert np.all(slope(errs["sync"])[-1] > p + 0.6)
+    assert np.all(slope(errs["at"])[-1] > p + 0.6)
+    # standard flux: the delay error takes over; its order keeps falling toward 1 and is
+    # well below the synchronous order on the finest meshes
+    s_std = slope(errs["std"])
+    assert np.all(s_std[-1] < 1.7)
+    assert np.all(s_std[-1] < slope(errs["sync"])[-1] - 0.3)
+    assert np.all(s_std[-1] < s_std[0])
+    assert np.all(errs["std"][-1] > 3 * errs["at"][-1])
+
+
+def test_reduced_precision_errors_match_fp64():
+    # L2 error against the exact vortex, same schedule and dt: FP32 pairs must match FP64;
+    # the FP32 operator's own rounding is reported beside the discretisation error
+    for n in (32, 128):
+        e64 = run(n, 2, "at", 0.05, "fp64", T=1.0)
+        edf = run(n, 2, "at", 0.05, "df64", T=1.0)
+        e32 = run(n, 2, "at", 0.05, "fp32", T=1.0)
+        print(f"{n}^2 p=2 AT t=1: fp64 {e64}, df64/fp64 {edf / e64}, fp32/fp64 {e32 / e64}")
+        np.testing.assert_allclose(edf, e64, rtol=1e-9)
+        assert np.all(np.abs(e32 / e64 - 1) < 0.05)
