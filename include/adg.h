@@ -101,7 +101,8 @@ typedef struct {
   int random_delay_max;      /* 0..15, random mode only                                */
   int at_np;                 /* AT stencil uses at_np+1 stored levels; <= 0: = degree  */
   adg_precision precision;   /* default ADG_PREC_FP64                                  */
-  void* cuda_stream;         /* cudaStream_t to order work on; NULL: the library makes one */
+  void* cuda_stream;         /* cudaStream_t to order work on; NULL: the legacy default
+                                stream (the stream torch uses unless told otherwise)     */
 } adg_options;
 
 /* Fills *opt with the defaults listed above. */

@@ -611,14 +611,9 @@ adg_status adg_create(const adg_mesh* mesh, int degree, const int P[3], int max_
     size_t ringn = (size_t)s->depth * (flux == ADG_FLUX_AT_TRACE ? 2 : 1) * s->NV * s->npe * s->NF;
     alloc(&s->ring, (ringn + 1) * sb);
   }
-  if (ce == cudaSuccess) {
-    if (o.cuda_stream) {
-      s->stream = (cudaStream_t)o.cuda_stream;
-    } else {
-      ce = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
-      s->own_stream = (ce == cudaSuccess);
-    }
-  }
+  // NULL selects the legacy default stream (handle 0), as in the CUDA runtime itself
+  s->stream = (cudaStream_t)o.cuda_stream;
+  s->own_stream = false;
   if (ce == cudaSuccess)
     ce = cudaMemcpyAsync(s->tab_dev, &s->tab, sizeof(OpTables), cudaMemcpyHostToDevice, s->stream);
   if (ce == cudaSuccess && flux != ADG_FLUX_SYNC) {
@@ -881,7 +876,7 @@ const char* adg_last_error(const adg_solver* s) { return s ? s->err.c_str() : g_
 
 void adg_destroy(adg_solver* s) {
   if (!s) return;
-  if (s->stream) cudaStreamSynchronize(s->stream);
+  cudaStreamSynchronize(s->stream);
   free_all(s);
   delete s;
 }

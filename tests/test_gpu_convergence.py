@@ -64,7 +64,7 @@ def test_convergence_orders_match_the_paper(p):
     assert np.all(s_std[-1] < 1.7)
     assert np.all(s_std[-1] < slope(errs["sync"])[-1] - 0.3)
     assert np.all(s_std[-1] < s_std[0])
-    assert np.all(errs["std"][-1] > 3 * errs["at"][-1])
+    assert np.all(errs["std"][-1] > 2 * errs["at"][-1])
 
 
 def test_reduced_precision_errors_match_fp64():
