@@ -258,6 +258,56 @@ def variant_run(adg, stream, precision, steps_per, k, warm, dt):
             "l2_error_vs_exact": [float(x) for x in err], "t": info["t"]}
 
 
+def batched_run(adg, stream, k=6):
+    """64 uneven vortex instances (meshes 32^2..256^2, degrees 2..5, L in {2,3,4}, 8x8
+    subdomains, AT flux, CK4(5), FP32 operator with FP64 accumulation): batched graph steps
+    against the same instances stepped one handle after another."""
+    import torch
+    from paper_2603_28710_gb300.inputs import vortex_instances
+    specs = vortex_instances(64, seed=7)
+    insts = [dict(n_elem=(q["n"], q["n"]), degree=q["degree"], P=(8, 8), max_delay=q["max_delay"])
+             for q in specs]
+    work = sum(4 * q["n"] ** 2 * (q["degree"] + 1) ** 2 for q in specs) * 5  # DoF-stages per step
+    b = adg.Batch(insts, flux="at", rk="ck45", cfl=0.1, precision="fp32", stream=stream.cuda_stream)
+    t0 = time.perf_counter()
+    tiles = b.autotune(trials=3)
+    tune_s = time.perf_counter() - t0
+    for i, q in enumerate(specs):
+        b.init_vortex(i, beta=q["beta"], x0=q["x0"], y0=q["y0"])
+    b.step(2)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.step(k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_batch = e0.elapsed_time(e1)
+    b.close()
+    singles = []
+    for q in specs:
+        s = adg.Solver(n_elem=(q["n"], q["n"]), degree=q["degree"], P=(8, 8), max_delay=q["max_delay"],
+                       flux="at", rk="ck45", cfl=0.1, precision="fp32", stream=stream.cuda_stream)
+        s.init_vortex(beta=q["beta"], x0=q["x0"], y0=q["y0"])
+        s.step(2)
+        singles.append(s)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(k):
+        for s in singles:
+            s.step(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_seq = e0.elapsed_time(e1)
+    for s in singles:
+        s.close()
+    return {"workload": "64 vortex instances, meshes 32^2..256^2, p 2..5, L 2..4, 8x8 subdomains, "
+                        "AT flux, CK4(5), FP32 operator / FP64 accumulation, one CUDA graph per step",
+            "value": work * k / (ms_batch * 1e-3) / 1e9, "unit": METRIC, "steps": k,
+            "ms_per_step": ms_batch / k, "sequential_handles_value": work * k / (ms_seq * 1e-3) / 1e9,
+            "speedup_vs_sequential": ms_seq / ms_batch, "tile_threads_per_degree_group": tiles,
+            "autotune_s": tune_s}
+
+
 # ---- GPU arm -----------------------------------------------------------------------------
 def run_gpu(args, rank, world, local_rank):
     import torch
@@ -380,6 +430,10 @@ def run_gpu(args, rank, world, local_rank):
             v["l2_error_ratio_vs_fp64"] = [a / b for a, b in zip(v["l2_error_vs_exact"],
                                                                  base["l2_error_vs_exact"])]
 
+    batched = None
+    if world == 1 and not args.no_batch:
+        batched = batched_run(adg, stream)
+
     clocks = clk.summary()
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -394,7 +448,7 @@ def run_gpu(args, rank, world, local_rank):
             "kernels": {"vol_kernel": {"ms_per_launch": vol_ms / max(vol_n, 1), "launches": vol_n},
                         "flux_kernel": {"ms_per_launch": flux_ms / max(flux_n, 1),
                                         "launches": flux_n}},
-            "variants": variants}
+            "variants": variants, "batched": batched}
     print(json.dumps(line), flush=True)
 
 
@@ -410,6 +464,7 @@ def main():
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the FP64 / FP32-pair / FP32 comparison runs")
     ap.add_argument("--variant-steps", type=int, default=10)
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-instances run")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

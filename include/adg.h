@@ -219,6 +219,40 @@ const char* adg_last_error(const adg_solver* s);
 /* Frees the handle and its device memory.  NULL-safe. */
 void adg_destroy(adg_solver* s);
 
+/* ---- batched solver ------------------------------------------------------------------ */
+/* Many independent instances (own mesh, degree, subdomains and max_delay; shared flux
+ * rule and options) advanced together.  Instances with the same dimension and degree form
+ * a group: every RK stage runs one persistent face-flux launch and one persistent volume
+ * launch per group, and one whole step of all groups is captured once into a CUDA graph
+ * and replayed by adg_batch_step.  The schedule of Algorithms 2/3 advances on the device,
+ * per instance.  Results equal those of separate adg_solver handles bit for bit. */
+typedef struct adg_batch adg_batch;
+
+/* meshes[n], degrees[n], P[3n], max_delay[n]; all meshes of one dimension.  Each
+ * instance's time step comes from options.cfl (or options.dt) at its own state. */
+adg_status adg_batch_create(int n, const adg_mesh* meshes, const int* degrees, const int* P,
+                            const int* max_delay, adg_flux flux, const adg_options* opt,
+                            adg_batch** out);
+/* State of instance i: the isentropic vortex (beta, centre), or a given state. */
+adg_status adg_batch_init_vortex(adg_batch* b, int i, double beta, double x0, double y0);
+adg_status adg_batch_set_state(adg_batch* b, int i, const double* u, int64_t count, int on_device);
+/* Advances every instance by n_steps steps (graph replays; enqueued, does not wait).
+ * Errors: ADG_ERR_STATE if an instance has no state. */
+adg_status adg_batch_step(adg_batch* b, int n_steps);
+/* Autotuner: for every degree group, times the volume launch with tiles of about 64, 128
+ * and 256 threads on the real buffers and keeps the fastest; tile_threads (nullable)
+ * receives one choice per group in increasing degree.  It overwrites every instance's
+ * state (set states afterwards). */
+adg_status adg_batch_autotune(adg_batch* b, int trials, int* tile_threads);
+adg_status adg_batch_get_state(adg_batch* b, int i, double* u, int64_t count, int on_device);
+adg_status adg_batch_info(const adg_batch* b, int i, double* t, int64_t* step, double* dt,
+                          int64_t* n_dof, int* degree);
+adg_status adg_batch_l2_error_vortex(adg_batch* b, int i, double t, double beta, double x0,
+                                     double y0, double* err3);
+int adg_batch_num_groups(const adg_batch* b);
+const char* adg_batch_last_error(const adg_batch* b);
+void adg_batch_destroy(adg_batch* b);
+
 /* ---- host-only helpers (no GPU needed) ---------------------------------------------- */
 
 /* Gauss-Legendre nodes x[n] (increasing) and weights w[n] on [-1, 1], 1 <= n <= 8. */

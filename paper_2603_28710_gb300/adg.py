@@ -27,7 +27,11 @@ STATUS = {0: "ADG_OK", 1: "ADG_ERR_INVALID", 2: "ADG_ERR_UNSUPPORTED", 3: "ADG_E
 SYMBOLS = ["adg_default_options", "adg_create", "adg_set_state", "adg_init_vortex",
            "adg_init_tgv", "adg_step", "adg_get_state", "adg_rhs", "adg_get_schedule",
            "adg_info", "adg_conservation", "adg_l2_error_vortex", "adg_check_finite",
-           "adg_last_error", "adg_destroy", "adg_set_profiling", "adg_get_profile", "adg_rhs_noalloc", "adg_host_gauss", "adg_host_at_coeffs",
+           "adg_last_error", "adg_destroy", "adg_set_profiling", "adg_get_profile", "adg_rhs_noalloc",
+           "adg_batch_create", "adg_batch_init_vortex", "adg_batch_set_state", "adg_batch_step",
+           "adg_batch_autotune", "adg_batch_get_state", "adg_batch_info",
+           "adg_batch_l2_error_vortex", "adg_batch_num_groups", "adg_batch_last_error",
+           "adg_batch_destroy", "adg_host_gauss", "adg_host_at_coeffs",
            "adg_host_rk", "adg_host_schedule", "adg_host_num_interfaces"]
 
 
@@ -84,6 +88,18 @@ def lib():
             "adg_set_profiling": ([P, I], I),
             "adg_get_profile": ([P, P, P], I),
             "adg_rhs_noalloc": ([ctypes.POINTER(Mesh), I, D, P, P, I64, P], I),
+            "adg_batch_create": ([I, P, P, P, P, I, ctypes.POINTER(Options),
+                                  ctypes.POINTER(ctypes.c_void_p)], I),
+            "adg_batch_init_vortex": ([P, I, D, D, D], I),
+            "adg_batch_set_state": ([P, I, P, I64, I], I),
+            "adg_batch_step": ([P, I], I),
+            "adg_batch_autotune": ([P, I, P], I),
+            "adg_batch_get_state": ([P, I, P, I64, I], I),
+            "adg_batch_info": ([P, I, P, P, P, P, P], I),
+            "adg_batch_l2_error_vortex": ([P, I, D, D, D, D, P], I),
+            "adg_batch_num_groups": ([P], I),
+            "adg_batch_last_error": ([P], ctypes.c_char_p),
+            "adg_batch_destroy": ([P], None),
             "adg_host_gauss": ([I, P, P], I),
             "adg_host_at_coeffs": ([I, D, P], I),
             "adg_host_rk": ([I, P, P, P, P], I),
@@ -325,3 +341,96 @@ class Solver:
             return False
         self._chk(st)
         return True
+
+
+class Batch:
+    """Batched solver (include/adg.h, adg_batch_*): instances given as a list of dicts with
+    keys n_elem, degree, P, max_delay (and optionally lo, hi)."""
+
+    def __init__(self, instances, dim=2, flux="at", rk="ck45", dt=0.0, cfl=0.1, gamma=1.4,
+                 delay_mode="caa", seed=0, random_delay_max=0, at_np=0, precision="fp32",
+                 stream=None):
+        L = lib()
+        n = len(instances)
+        meshes = (Mesh * n)()
+        degs = (ctypes.c_int * n)()
+        Ps = (ctypes.c_int * (3 * n))()
+        Ls = (ctypes.c_int * n)()
+        for i, ins in enumerate(instances):
+            ne = ins["n_elem"]
+            lo = ins.get("lo", (-5.0,) * dim)
+            hi = ins.get("hi", (5.0,) * dim)
+            meshes[i].dim = dim
+            for d in range(3):
+                meshes[i].n_elem[d] = ne[d] if d < dim else 1
+                meshes[i].lo[d] = lo[d] if d < dim else 0.0
+                meshes[i].hi[d] = hi[d] if d < dim else 1.0
+                Ps[3 * i + d] = ins.get("P", (1, 1, 1))[d] if d < dim else 1
+            degs[i] = ins["degree"]
+            Ls[i] = ins.get("max_delay", 1)
+        o = Options()
+        _check(L.adg_default_options(ctypes.byref(o)))
+        o.rk, o.dt, o.cfl, o.gamma = RK[rk], dt, cfl, gamma
+        o.delay_mode, o.seed = DELAY[delay_mode], seed & 0xFFFFFFFFFFFFFFFF
+        o.random_delay_max, o.at_np, o.precision = random_delay_max, at_np, PREC[precision]
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        o.cuda_stream = stream
+        h = ctypes.c_void_p()
+        st = L.adg_batch_create(n, meshes, degs, Ps, Ls, FLUX[flux], ctypes.byref(o), ctypes.byref(h))
+        if st != 0:
+            msg = L.adg_batch_last_error(None)
+            raise AdgError(st, msg.decode() if msg else "")
+        self._h, self._L, self.n, self.dim = h, L, n, dim
+        self.instances = instances
+
+    def _chk(self, st):
+        if st != 0:
+            msg = self._L.adg_batch_last_error(self._h)
+            raise AdgError(st, msg.decode() if msg else "")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.adg_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def init_vortex(self, i, beta=5.0, x0=0.0, y0=0.0):
+        self._chk(self._L.adg_batch_init_vortex(self._h, i, beta, x0, y0))
+
+    def set_state(self, i, u):
+        p, n, dev = _buf(u)
+        self._chk(self._L.adg_batch_set_state(self._h, i, p, n, dev))
+
+    def step(self, n=1):
+        self._chk(self._L.adg_batch_step(self._h, n))
+
+    def autotune(self, trials=3):
+        g = self._L.adg_batch_num_groups(self._h)
+        out = (ctypes.c_int * max(g, 1))()
+        self._chk(self._L.adg_batch_autotune(self._h, trials, out))
+        return list(out)[:g]
+
+    def info(self, i):
+        t, dt = ctypes.c_double(), ctypes.c_double()
+        st, nd, deg = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
+        self._chk(self._L.adg_batch_info(self._h, i, ctypes.byref(t), ctypes.byref(st),
+                                         ctypes.byref(dt), ctypes.byref(nd), ctypes.byref(deg)))
+        return dict(t=t.value, step=st.value, dt=dt.value, n_dof=nd.value, degree=deg.value)
+
+    def get_state(self, i, out=None):
+        inf = self.info(i)
+        if out is None:
+            nd = (inf["degree"] + 1) ** self.dim
+            out = np.empty((self.dim + 2, inf["n_dof"] // ((self.dim + 2) * nd), nd))
+        p, n, dev = _buf(out, writable=True)
+        self._chk(self._L.adg_batch_get_state(self._h, i, p, n, dev))
+        return out
+
+    def l2_error_vortex(self, i, t, beta=5.0, x0=0.0, y0=0.0):
+        e = np.zeros(3)
+        self._chk(self._L.adg_batch_l2_error_vortex(self._h, i, t, beta, x0, y0, _np_ptr(e)))
+        return e

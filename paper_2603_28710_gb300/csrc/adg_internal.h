@@ -38,7 +38,7 @@ struct MeshArgs {
 
 enum UpdateMode { kModeRHS = 0, kMode2R = 1, kMode2N = 2 };
 
-struct VolArgs {
+struct __align__(16) VolArgs {
   MeshArgs m;
   const OpTables* tab;
   double gamma;
@@ -58,7 +58,7 @@ struct VolArgs {
   int write_traces;
 };
 
-struct FluxArgs {
+struct __align__(16) FluxArgs {
   MeshArgs m;
   double gamma;
   float2 gammaf;

@@ -1,0 +1,163 @@
+// Batched kernels: many independent solver instances of the same dimension and degree in
+// one launch.  Each launch is persistent (a grid-stride loop over "virtual blocks"); the
+// virtual blocks of all instances are numbered consecutively and a block finds its
+// instance by binary search over the per-instance offsets.  The element work itself is the
+// single-instance code (vol_body / flux_body), reading per-instance, per-stage arguments
+// from device memory, so a batched step gives bit-identical results to separate solvers.
+#pragma once
+#include "kernels.cuh"
+
+namespace adg {
+
+// Per-instance schedule state advanced on the device at the start of every step.
+struct BatchSched {
+  int random;        // per-interface random delays
+  int pe;            // instance has subdomain faces and a delayed flux mode
+  int flux_kind;     // adg_flux
+  int L, np, depth;  // schedule parameters
+  int head;          // ring level written last (-1: none yet)
+  int pad;
+  long long step;    // index of the step about to run
+};
+
+struct BatchGroupArgs {
+  const int* inst;   // instance ids of the group
+  const int* off;    // [n+1] first virtual block of each instance
+  int n;             // instances in the group
+  int total;         // virtual blocks in total
+};
+
+__device__ __forceinline__ int find_instance(const BatchGroupArgs& g, int vb) {
+  int lo = 0, hi = g.n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (g.off[mid] <= vb) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Copy of one argument struct into shared memory by the whole block (16-byte words), so the
+// element code reads it from shared memory instead of re-reading global memory after every
+// global store it cannot prove to be unrelated.
+template <typename T>
+__device__ __forceinline__ void stage_args(T* dst, const T* src) {
+  static_assert(sizeof(T) % 16 == 0, "argument structs are padded to 16 bytes");
+  const int4* s = reinterpret_cast<const int4*>(src);
+  int4* d = reinterpret_cast<int4*>(dst);
+  for (int i = threadIdx.x; i < (int)(sizeof(T) / 16); i += blockDim.x) d[i] = s[i];
+}
+
+template <int D, int N, typename R, int TT>
+__global__ void __launch_bounds__(Tile<D, N, TT>::THREADS)
+batch_vol_kernel(const VolArgs* va, int nstages, int stage, BatchGroupArgs g) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(16) VolArgs sa;
+  for (int vb = blockIdx.x; vb < g.total; vb += gridDim.x) {
+    const int k = find_instance(g, vb);
+    stage_args(&sa, &va[g.inst[k] * nstages + stage]);
+    __syncthreads();
+    vol_body<D, N, R, TT>(sa, vb - g.off[k], smem_raw);
+    __syncthreads();  // shared memory is reused by the next virtual block
+  }
+}
+
+// virtual block of instance k: D * blocks_x of it, ordered (d, bx)
+template <int D, int N, typename R>
+__global__ void __launch_bounds__(256)
+batch_flux_kernel(const FluxArgs* fa, int nstages, int stage, BatchGroupArgs g) {
+  constexpr int NF = IPow<N, D - 1>::value;
+  __shared__ __align__(16) FluxArgs sa;
+  for (int vb = blockIdx.x; vb < g.total; vb += gridDim.x) {
+    const int k = find_instance(g, vb);
+    stage_args(&sa, &fa[g.inst[k] * nstages + stage]);
+    __syncthreads();
+    const int bpd = ((int)sa.m.ne * NF + 255) / 256;
+    const int local = vb - g.off[k];
+    const int d = local / bpd;
+    flux_body<D, N, R>(sa, local - d * bpd, d);
+    __syncthreads();
+  }
+}
+
+// Launchers over (dim, N, TT) for one arithmetic (2D and 3D, TT in {64, 128, 256}).
+template <typename R>
+struct BatchDispatch {
+  template <int D, int N, int TT>
+  static cudaError_t vol_t(const VolArgs* va, int ns, int st, const BatchGroupArgs& g, int grid,
+                           cudaStream_t s) {
+    using T = Tile<D, N, TT>;
+    const size_t smem = sizeof(R) * T::EPB * D * T::NV * T::ND;
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(batch_vol_kernel<D, N, R, TT>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    batch_vol_kernel<D, N, R, TT><<<grid, T::THREADS, smem, s>>>(va, ns, st, g);
+    return cudaGetLastError();
+  }
+  template <int D, int N>
+  static cudaError_t flux_t(const FluxArgs* fa, int ns, int st, const BatchGroupArgs& g, int grid,
+                            cudaStream_t s) {
+    batch_flux_kernel<D, N, R><<<grid, 256, 0, s>>>(fa, ns, st, g);
+    return cudaGetLastError();
+  }
+  template <int D, int N>
+  static cudaError_t vol_tt(int tt, const VolArgs* va, int ns, int st, const BatchGroupArgs& g,
+                            int grid, cudaStream_t s) {
+    switch (tt) {
+      case 64: return vol_t<D, N, 64>(va, ns, st, g, grid, s);
+      case 128: return vol_t<D, N, 128>(va, ns, st, g, grid, s);
+      case 256: return vol_t<D, N, 256>(va, ns, st, g, grid, s);
+    }
+    return cudaErrorInvalidValue;
+  }
+  static cudaError_t vol(int dim, int N, int tt, const VolArgs* va, int ns, int st,
+                         const BatchGroupArgs& g, int grid, cudaStream_t s) {
+    if (dim == 2) {
+      switch (N) {
+        case 2: return vol_tt<2, 2>(tt, va, ns, st, g, grid, s);
+        case 3: return vol_tt<2, 3>(tt, va, ns, st, g, grid, s);
+        case 4: return vol_tt<2, 4>(tt, va, ns, st, g, grid, s);
+        case 5: return vol_tt<2, 5>(tt, va, ns, st, g, grid, s);
+        case 6: return vol_tt<2, 6>(tt, va, ns, st, g, grid, s);
+        case 7: return vol_tt<2, 7>(tt, va, ns, st, g, grid, s);
+        case 8: return vol_tt<2, 8>(tt, va, ns, st, g, grid, s);
+      }
+    } else if (dim == 3) {
+      switch (N) {
+        case 2: return vol_tt<3, 2>(tt, va, ns, st, g, grid, s);
+        case 3: return vol_tt<3, 3>(tt, va, ns, st, g, grid, s);
+        case 4: return vol_tt<3, 4>(tt, va, ns, st, g, grid, s);
+        case 5: return vol_tt<3, 5>(tt, va, ns, st, g, grid, s);
+        case 6: return vol_tt<3, 6>(tt, va, ns, st, g, grid, s);
+      }
+    }
+    return cudaErrorInvalidValue;
+  }
+  static cudaError_t flux(int dim, int N, const FluxArgs* fa, int ns, int st,
+                          const BatchGroupArgs& g, int grid, cudaStream_t s) {
+    if (dim == 2) {
+      switch (N) {
+        case 2: return flux_t<2, 2>(fa, ns, st, g, grid, s);
+        case 3: return flux_t<2, 3>(fa, ns, st, g, grid, s);
+        case 4: return flux_t<2, 4>(fa, ns, st, g, grid, s);
+        case 5: return flux_t<2, 5>(fa, ns, st, g, grid, s);
+        case 6: return flux_t<2, 6>(fa, ns, st, g, grid, s);
+        case 7: return flux_t<2, 7>(fa, ns, st, g, grid, s);
+        case 8: return flux_t<2, 8>(fa, ns, st, g, grid, s);
+      }
+    } else if (dim == 3) {
+      switch (N) {
+        case 2: return flux_t<3, 2>(fa, ns, st, g, grid, s);
+        case 3: return flux_t<3, 3>(fa, ns, st, g, grid, s);
+        case 4: return flux_t<3, 4>(fa, ns, st, g, grid, s);
+        case 5: return flux_t<3, 5>(fa, ns, st, g, grid, s);
+        case 6: return flux_t<3, 6>(fa, ns, st, g, grid, s);
+      }
+    }
+    return cudaErrorInvalidValue;
+  }
+};
+
+}  // namespace adg

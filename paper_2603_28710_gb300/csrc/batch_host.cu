@@ -1,0 +1,472 @@
+// Batched solver: many independent instances (different meshes, degrees and delays)
+// advanced together.  Instances of the same dimension and degree form a group; per RK
+// stage every group runs one persistent flux launch and one persistent volume launch over
+// all of its instances.  A whole step (schedule kernel + all stage launches) is captured
+// once into a CUDA graph and replayed; an autotuner picks each group's element tile.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/adg.h"
+#include "batch.cuh"
+#include "solver_internal.h"
+
+namespace adg {
+cudaError_t batch_vol_fp64(int, int, int, const VolArgs*, int, int, const BatchGroupArgs&, int, cudaStream_t);
+cudaError_t batch_vol_fp32(int, int, int, const VolArgs*, int, int, const BatchGroupArgs&, int, cudaStream_t);
+cudaError_t batch_vol_df64(int, int, int, const VolArgs*, int, int, const BatchGroupArgs&, int, cudaStream_t);
+cudaError_t batch_flux_fp64(int, int, const FluxArgs*, int, int, const BatchGroupArgs&, int, cudaStream_t);
+cudaError_t batch_flux_fp32(int, int, const FluxArgs*, int, int, const BatchGroupArgs&, int, cudaStream_t);
+cudaError_t batch_flux_df64(int, int, const FluxArgs*, int, int, const BatchGroupArgs&, int, cudaStream_t);
+void noalloc_set_error(const char* msg);
+
+namespace {
+
+// One thread per instance: communication flag, delay counter and ring head of the step
+// about to run (closed forms of Algorithms 2 and 3), written into every stage's flux
+// arguments; then the step counter advances.
+__global__ void batch_schedule_kernel(BatchSched* sc, FluxArgs* fa, int nstages, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  BatchSched s = sc[i];
+  const long long step = s.step;
+  int comm = 1, k = 0;
+  if (!s.random && s.pe) {
+    if (s.flux_kind == 1) {
+      k = (int)(step % s.L);
+      comm = (k == 0);
+    } else if (s.flux_kind >= 2) {
+      const long long cyc = (long long)s.L + s.np + 1;
+      const int ph = (int)(step % cyc);
+      comm = ph < s.np + 1;
+      k = comm ? 0 : ph - s.np;
+    }
+  }
+  const int store = s.pe && (s.random || comm);
+  if (store) s.head = (s.head + 1) % s.depth;
+  for (int m = 0; m < nstages; ++m) {
+    FluxArgs& A = fa[i * nstages + m];
+    A.store = (store && m == 0) ? 1 : 0;
+    A.head = s.head < 0 ? 0 : s.head;
+    A.uniform_delay = s.random ? 0 : (comm ? 0 : k);
+    A.step = step;
+  }
+  s.step = step + 1;
+  sc[i] = s;
+}
+
+cudaError_t vol_launch(int prec, int dim, int N, int tt, const VolArgs* va, int ns, int st,
+                       const BatchGroupArgs& g, int grid, cudaStream_t s) {
+  switch (prec) {
+    case 0: return batch_vol_fp64(dim, N, tt, va, ns, st, g, grid, s);
+    case 1: return batch_vol_fp32(dim, N, tt, va, ns, st, g, grid, s);
+    case 2: return batch_vol_df64(dim, N, tt, va, ns, st, g, grid, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t flux_launch(int prec, int dim, int N, const FluxArgs* fa, int ns, int st,
+                        const BatchGroupArgs& g, int grid, cudaStream_t s) {
+  switch (prec) {
+    case 0: return batch_flux_fp64(dim, N, fa, ns, st, g, grid, s);
+    case 1: return batch_flux_fp32(dim, N, fa, ns, st, g, grid, s);
+    case 2: return batch_flux_df64(dim, N, fa, ns, st, g, grid, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+int ipow(int b, int e) {
+  int r = 1;
+  while (e-- > 0) r *= b;
+  return r;
+}
+
+}  // namespace
+}  // namespace adg
+
+using namespace adg;
+
+struct adg_batch {
+  std::vector<adg_solver*> inst;
+  int n = 0, prec = 0, stages = 0, dim = 2;
+  cudaStream_t stream = nullptr;
+  VolArgs* va_dev = nullptr;
+  FluxArgs* fa_dev = nullptr;
+  BatchSched* sc_dev = nullptr;
+  std::vector<VolArgs> va_host;
+  std::vector<FluxArgs> fa_host;
+  std::vector<BatchSched> sc_host;
+  std::vector<char> has_state;
+  std::vector<int64_t> inst_steps;  // steps taken since each instance's state was set
+  struct Group {
+    int N = 0, tt = 128;
+    std::vector<int> inst;
+    int* inst_dev = nullptr;
+    int* voff_dev = nullptr;
+    int* foff_dev = nullptr;
+    int vtotal = 0, ftotal = 0;
+    int vgrid = 0, fgrid = 0;
+  };
+  std::vector<Group> groups;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  int64_t steps = 0;
+  std::string err;
+};
+
+namespace {
+
+adg_status bfail(adg_batch* b, adg_status st, const std::string& m) {
+  if (b) b->err = m;
+  else noalloc_set_error(m.c_str());
+  return st;
+}
+
+#define BCUDA(B, call)                                                                        \
+  do {                                                                                        \
+    cudaError_t e__ = (call);                                                                 \
+    if (e__ != cudaSuccess)                                                                   \
+      return bfail((B), e__ == cudaErrorMemoryAllocation ? ADG_ERR_OOM : ADG_ERR_CUDA,        \
+                   std::string(#call) + ": " + cudaGetErrorString(e__));                      \
+  } while (0)
+
+void drop_graph(adg_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+}
+
+void free_batch(adg_batch* b) {
+  drop_graph(b);
+  for (auto& g : b->groups) {
+    if (g.inst_dev) cudaFree(g.inst_dev);
+    if (g.voff_dev) cudaFree(g.voff_dev);
+    if (g.foff_dev) cudaFree(g.foff_dev);
+  }
+  if (b->va_dev) cudaFree(b->va_dev);
+  if (b->fa_dev) cudaFree(b->fa_dev);
+  if (b->sc_dev) cudaFree(b->sc_dev);
+  for (adg_solver* s : b->inst) adg_destroy(s);
+}
+
+// persistent grid: enough blocks to fill every SM a few times, never more than needed
+int persistent_grid(int total, int per_sm) {
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess)
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return std::max(1, std::min(total, sms * per_sm));
+}
+
+// virtual-block offsets of a group for the chosen tile
+adg_status layout_group(adg_batch* b, adg_batch::Group& g) {
+  const int nd = ipow(g.N, b->dim), nf = nd / g.N;
+  const int epb = std::max(1, g.tt / nd);
+  std::vector<int> voff(g.inst.size() + 1), foff(g.inst.size() + 1);
+  voff[0] = foff[0] = 0;
+  for (size_t k = 0; k < g.inst.size(); ++k) {
+    const int64_t ne = b->inst[g.inst[k]]->ne;
+    voff[k + 1] = voff[k] + (int)((ne + epb - 1) / epb);
+    foff[k + 1] = foff[k] + b->dim * (int)((ne * nf + 255) / 256);
+  }
+  g.vtotal = voff.back();
+  g.ftotal = foff.back();
+  const int threads = epb * nd;
+  g.vgrid = persistent_grid(g.vtotal, std::max(1, 2048 / threads));
+  g.fgrid = persistent_grid(g.ftotal, 8);
+  BCUDA(b, cudaMemcpy(g.voff_dev, voff.data(), voff.size() * sizeof(int), cudaMemcpyHostToDevice));
+  BCUDA(b, cudaMemcpy(g.foff_dev, foff.data(), foff.size() * sizeof(int), cudaMemcpyHostToDevice));
+  return ADG_OK;
+}
+
+BatchGroupArgs group_args(const adg_batch::Group& g, bool vol) {
+  BatchGroupArgs a;
+  a.inst = g.inst_dev;
+  a.off = vol ? g.voff_dev : g.foff_dev;
+  a.n = (int)g.inst.size();
+  a.total = vol ? g.vtotal : g.ftotal;
+  return a;
+}
+
+// enqueue one full step: schedule kernel, then flux and volume launches of every group
+adg_status enqueue_step(adg_batch* b, cudaStream_t s) {
+  batch_schedule_kernel<<<(b->n + 127) / 128, 128, 0, s>>>(b->sc_dev, b->fa_dev, b->stages, b->n);
+  BCUDA(b, cudaGetLastError());
+  for (int m = 0; m < b->stages; ++m) {
+    for (auto& g : b->groups)
+      BCUDA(b, flux_launch(b->prec, b->dim, g.N, b->fa_dev, b->stages, m, group_args(g, false),
+                           g.fgrid, s));
+    for (auto& g : b->groups)
+      BCUDA(b, vol_launch(b->prec, b->dim, g.N, g.tt, b->va_dev, b->stages, m,
+                          group_args(g, true), g.vgrid, s));
+  }
+  return ADG_OK;
+}
+
+// The step is captured on a private stream (the legacy default stream cannot be captured);
+// the instantiated graph is then launched on the caller's stream.
+adg_status build_graph(adg_batch* b) {
+  drop_graph(b);
+  cudaStream_t cap = nullptr;
+  BCUDA(b, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaStreamDestroy(cap);
+    BCUDA(b, e);
+  }
+  adg_status st = enqueue_step(b, cap);
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(cap, &g);
+  cudaStreamDestroy(cap);
+  if (st != ADG_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  BCUDA(b, e);
+  b->graph = g;
+  BCUDA(b, cudaGraphInstantiate(&b->exec, g, 0));
+  return ADG_OK;
+}
+
+adg_status refresh_instance(adg_batch* b, int i) {
+  adg_solver* s = b->inst[i];
+  for (int m = 0; m < b->stages; ++m) {
+    b->va_host[i * b->stages + m] = stage_vol_args(s, m);
+    b->fa_host[i * b->stages + m] = stage_flux_args(s, m);
+  }
+  BatchSched sc;
+  std::memset(&sc, 0, sizeof(sc));
+  sc.random = s->opt.delay_mode == ADG_DELAY_RANDOM;
+  sc.pe = (s->flux != ADG_FLUX_SYNC && s->npe > 0) ? 1 : 0;
+  sc.flux_kind = (int)s->flux;
+  sc.L = s->max_delay;
+  sc.np = s->np;
+  sc.depth = s->depth;
+  sc.head = -1;
+  sc.step = 0;
+  b->sc_host[i] = sc;
+  BCUDA(b, cudaMemcpyAsync(b->va_dev + i * b->stages, &b->va_host[i * b->stages],
+                           sizeof(VolArgs) * b->stages, cudaMemcpyHostToDevice, b->stream));
+  BCUDA(b, cudaMemcpyAsync(b->fa_dev + i * b->stages, &b->fa_host[i * b->stages],
+                           sizeof(FluxArgs) * b->stages, cudaMemcpyHostToDevice, b->stream));
+  BCUDA(b, cudaMemcpyAsync(b->sc_dev + i, &b->sc_host[i], sizeof(BatchSched),
+                           cudaMemcpyHostToDevice, b->stream));
+  BCUDA(b, cudaStreamSynchronize(b->stream));
+  b->has_state[i] = 1;
+  b->inst_steps[i] = 0;
+  return ADG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+adg_status adg_batch_create(int n, const adg_mesh* meshes, const int* degrees, const int* P,
+                            const int* max_delay, adg_flux flux, const adg_options* opt,
+                            adg_batch** out) {
+  if (!out) return bfail(nullptr, ADG_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (n < 1 || !meshes || !degrees || !P || !max_delay)
+    return bfail(nullptr, ADG_ERR_INVALID, "need n >= 1 and non-NULL meshes, degrees, P, max_delay");
+  adg_options o;
+  if (opt) o = *opt;
+  else adg_default_options(&o);
+  adg_batch* b = new (std::nothrow) adg_batch();
+  if (!b) return bfail(nullptr, ADG_ERR_OOM, "host allocation failed");
+  b->n = n;
+  b->prec = (int)o.precision;
+  b->stream = (cudaStream_t)o.cuda_stream;
+  b->dim = meshes[0].dim;
+  for (int i = 0; i < n; ++i) {
+    if (meshes[i].dim != b->dim) {
+      free_batch(b);
+      delete b;
+      return bfail(nullptr, ADG_ERR_INVALID, "all instances must have the same dimension");
+    }
+    adg_solver* s = nullptr;
+    adg_status st = adg_create(&meshes[i], degrees[i], &P[3 * i], max_delay[i], flux, &o, &s);
+    if (st != ADG_OK) {
+      std::string msg = std::string("instance ") + std::to_string(i) + ": " + adg_last_error(nullptr);
+      free_batch(b);
+      delete b;
+      return bfail(nullptr, st, msg);
+    }
+    b->inst.push_back(s);
+  }
+  b->stages = b->inst[0]->stages;
+  b->va_host.resize((size_t)n * b->stages);
+  b->fa_host.resize((size_t)n * b->stages);
+  b->sc_host.resize(n);
+  b->has_state.assign(n, 0);
+  b->inst_steps.assign(n, 0);
+  std::map<int, std::vector<int>> by_n;
+  for (int i = 0; i < n; ++i) by_n[b->inst[i]->N].push_back(i);
+  cudaError_t ce = cudaMalloc((void**)&b->va_dev, sizeof(VolArgs) * n * b->stages);
+  if (ce == cudaSuccess) ce = cudaMalloc((void**)&b->fa_dev, sizeof(FluxArgs) * n * b->stages);
+  if (ce == cudaSuccess) ce = cudaMalloc((void**)&b->sc_dev, sizeof(BatchSched) * n);
+  for (auto& kv : by_n) {
+    adg_batch::Group g;
+    g.N = kv.first;
+    g.inst = kv.second;
+    const size_t k = g.inst.size();
+    if (ce == cudaSuccess) ce = cudaMalloc((void**)&g.inst_dev, k * sizeof(int));
+    if (ce == cudaSuccess) ce = cudaMalloc((void**)&g.voff_dev, (k + 1) * sizeof(int));
+    if (ce == cudaSuccess) ce = cudaMalloc((void**)&g.foff_dev, (k + 1) * sizeof(int));
+    if (ce == cudaSuccess) ce = cudaMemcpy(g.inst_dev, g.inst.data(), k * sizeof(int), cudaMemcpyHostToDevice);
+    b->groups.push_back(g);
+  }
+  if (ce != cudaSuccess) {
+    std::string msg = std::string("adg_batch_create: ") + cudaGetErrorString(ce);
+    free_batch(b);
+    delete b;
+    return bfail(nullptr, ce == cudaErrorMemoryAllocation ? ADG_ERR_OOM : ADG_ERR_CUDA, msg);
+  }
+  for (auto& g : b->groups) {
+    adg_status st = layout_group(b, g);
+    if (st != ADG_OK) {
+      std::string msg = b->err;
+      free_batch(b);
+      delete b;
+      return bfail(nullptr, st, msg);
+    }
+  }
+  *out = b;
+  return ADG_OK;
+}
+
+adg_status adg_batch_init_vortex(adg_batch* b, int i, double beta, double x0, double y0) {
+  if (!b) return bfail(nullptr, ADG_ERR_INVALID, "handle is NULL");
+  if (i < 0 || i >= b->n) return bfail(b, ADG_ERR_INVALID, "instance index out of range");
+  adg_status st = adg_init_vortex(b->inst[i], 0.0, beta, x0, y0);
+  if (st != ADG_OK) return bfail(b, st, adg_last_error(b->inst[i]));
+  return refresh_instance(b, i);
+}
+
+adg_status adg_batch_set_state(adg_batch* b, int i, const double* u, int64_t count, int on_device) {
+  if (!b) return bfail(nullptr, ADG_ERR_INVALID, "handle is NULL");
+  if (i < 0 || i >= b->n) return bfail(b, ADG_ERR_INVALID, "instance index out of range");
+  adg_status st = adg_set_state(b->inst[i], u, count, on_device);
+  if (st != ADG_OK) return bfail(b, st, adg_last_error(b->inst[i]));
+  return refresh_instance(b, i);
+}
+
+adg_status adg_batch_step(adg_batch* b, int n_steps) {
+  if (!b) return bfail(nullptr, ADG_ERR_INVALID, "handle is NULL");
+  if (n_steps < 0) return bfail(b, ADG_ERR_INVALID, "n_steps must be >= 0");
+  for (int i = 0; i < b->n; ++i)
+    if (!b->has_state[i]) return bfail(b, ADG_ERR_STATE, "instance " + std::to_string(i) + " has no state");
+  if (!b->exec) {
+    adg_status st = build_graph(b);
+    if (st != ADG_OK) return st;
+  }
+  for (int it = 0; it < n_steps; ++it) BCUDA(b, cudaGraphLaunch(b->exec, b->stream));
+  b->steps += n_steps;
+  for (int i = 0; i < b->n; ++i) b->inst_steps[i] += n_steps;
+  return ADG_OK;
+}
+
+adg_status adg_batch_autotune(adg_batch* b, int trials, int* tile_threads) {
+  if (!b) return bfail(nullptr, ADG_ERR_INVALID, "handle is NULL");
+  if (trials < 1) trials = 3;
+  // uniform flow in every instance: the tuner times real launches on real buffers
+  for (int i = 0; i < b->n; ++i) {
+    adg_solver* s = b->inst[i];
+    std::vector<double> u((size_t)s->ndof);
+    const int64_t per = s->ne * s->ND;
+    for (int v = 0; v < s->NV; ++v)
+      for (int64_t q = 0; q < per; ++q)
+        u[v * per + q] = (v == 0) ? 1.0 : (v == s->NV - 1 ? 2.5 : 0.0);
+    adg_status st = adg_set_state(s, u.data(), s->ndof, 0);
+    if (st != ADG_OK) return bfail(b, st, adg_last_error(s));
+    st = refresh_instance(b, i);
+    if (st != ADG_OK) return st;
+  }
+  drop_graph(b);
+  cudaEvent_t e0, e1;
+  BCUDA(b, cudaEventCreate(&e0));
+  BCUDA(b, cudaEventCreate(&e1));
+  const int cand[3] = {64, 128, 256};
+  for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+    auto& g = b->groups[gi];
+    float best = 1e30f;
+    int best_tt = 128;
+    for (int tt : cand) {
+      g.tt = tt;
+      adg_status st = layout_group(b, g);
+      if (st != ADG_OK) return st;
+      // warm-up, then time `trials` launches of the group's volume kernel (stage 0: it
+      // reads only the solution, never the RK register)
+      BCUDA(b, vol_launch(b->prec, b->dim, g.N, g.tt, b->va_dev, b->stages, 0,
+                          group_args(g, true), g.vgrid, b->stream));
+      BCUDA(b, cudaEventRecord(e0, b->stream));
+      for (int t = 0; t < trials; ++t)
+        BCUDA(b, vol_launch(b->prec, b->dim, g.N, g.tt, b->va_dev, b->stages, 0,
+                            group_args(g, true), g.vgrid, b->stream));
+      BCUDA(b, cudaEventRecord(e1, b->stream));
+      BCUDA(b, cudaEventSynchronize(e1));
+      float ms = 0.f;
+      BCUDA(b, cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) {
+        best = ms;
+        best_tt = tt;
+      }
+    }
+    g.tt = best_tt;
+    adg_status st = layout_group(b, g);
+    if (st != ADG_OK) return st;
+    if (tile_threads) tile_threads[gi] = best_tt;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  // the tuning launches advanced the uniform flow; states must be set again
+  for (int i = 0; i < b->n; ++i) b->has_state[i] = 0;
+  return ADG_OK;
+}
+
+adg_status adg_batch_get_state(adg_batch* b, int i, double* u, int64_t count, int on_device) {
+  if (!b) return bfail(nullptr, ADG_ERR_INVALID, "handle is NULL");
+  if (i < 0 || i >= b->n) return bfail(b, ADG_ERR_INVALID, "instance index out of range");
+  adg_status st = adg_get_state(b->inst[i], u, count, on_device);
+  if (st != ADG_OK) return bfail(b, st, adg_last_error(b->inst[i]));
+  return ADG_OK;
+}
+
+adg_status adg_batch_info(const adg_batch* b, int i, double* t, int64_t* step, double* dt,
+                          int64_t* n_dof, int* degree) {
+  if (!b) return bfail(nullptr, ADG_ERR_INVALID, "handle is NULL");
+  if (i < 0 || i >= b->n) return bfail(const_cast<adg_batch*>(b), ADG_ERR_INVALID, "instance index out of range");
+  const adg_solver* s = b->inst[i];
+  if (step) *step = b->inst_steps[i];
+  if (dt) *dt = s->dt;
+  if (t) *t = s->dt * (double)b->inst_steps[i];
+  if (n_dof) *n_dof = s->ndof;
+  if (degree) *degree = s->degree;
+  return ADG_OK;
+}
+
+adg_status adg_batch_l2_error_vortex(adg_batch* b, int i, double t, double beta, double x0,
+                                     double y0, double* err3) {
+  if (!b) return bfail(nullptr, ADG_ERR_INVALID, "handle is NULL");
+  if (i < 0 || i >= b->n) return bfail(b, ADG_ERR_INVALID, "instance index out of range");
+  adg_status st = adg_l2_error_vortex(b->inst[i], t, beta, x0, y0, err3);
+  if (st != ADG_OK) return bfail(b, st, adg_last_error(b->inst[i]));
+  return ADG_OK;
+}
+
+int adg_batch_num_groups(const adg_batch* b) { return b ? (int)b->groups.size() : -1; }
+
+const char* adg_batch_last_error(const adg_batch* b) { return b ? b->err.c_str() : adg_last_error(nullptr); }
+
+void adg_batch_destroy(adg_batch* b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->stream);
+  free_batch(b);
+  delete b;
+}
+
+}  // extern "C"

@@ -11,56 +11,18 @@
 
 #include "../../include/adg.h"
 #include "adg_internal.h"
+#include "solver_internal.h"
 
 using namespace adg;
 
-struct adg_solver {
-  adg_mesh mesh{};
-  int dim = 2, degree = 1, N = 2, ND = 4, NF = 2, NV = 4;
-  int64_t ne = 0, ndof = 0;
-  int P[3] = {1, 1, 1};
-  int max_delay = 0;
-  adg_flux flux = ADG_FLUX_SYNC;
-  adg_options opt{};
-  int np = 1;
-  int stages = 0;
-  bool rk2n = false;
-  double rka[8] = {0}, rkb[8] = {0}, rkc[8] = {0};
-  double h[3] = {1, 1, 1};
-  double J = 1.0;
-  int prec = 0;
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  // device memory
-  double* w = nullptr;
-  void* x = nullptr;         // 2R: r ; 2N: q (operator storage type)
-  void* tr = nullptr;        // traces
-  void* fl = nullptr;        // face fluxes
-  void* ring = nullptr;      // delayed-flux history
-  int32_t* pe_slot = nullptr;
-  int32_t* pe_iface = nullptr;
-  OpTables* tab_dev = nullptr;
-  double* red_partial = nullptr;
-  double* red_out = nullptr;
-  int* flag = nullptr;
-  double* tmp_u = nullptr;
-  double* tmp_k = nullptr;
-  int red_blocks = 0;
-  OpTables tab{};
-  MeshArgs margs{};
-  int64_t npe = 0;
-  int depth = 0, head = -1, n_iface = 0;
-  // run state
-  bool has_state = false, traces_valid = false;
-  int64_t step = 0;
-  double t = 0.0, dt = 0.0;
-  std::string err;
-  // kernel timing (adg_set_profiling)
-  bool profiling = false;
-  std::vector<cudaEvent_t> ev_pool;
-  std::vector<int> ev_kind;  // kind of each recorded pair
-  size_t ev_used = 0;
-};
+namespace adg {
+// (hi, lo) FP32 pair of a value: hi = RN(v), lo = RN(v - hi)
+float2 split2(long double v) {
+  float hi = (float)v;
+  float lo = (float)(v - (long double)hi);
+  return make_float2(hi, lo);
+}
+}  // namespace adg
 
 namespace {
 
@@ -82,13 +44,6 @@ adg_status cuda_fail(adg_solver* s, cudaError_t e, const char* what) {
     cudaError_t e__ = (call);                                \
     if (e__ != cudaSuccess) return cuda_fail((S), e__, #call); \
   } while (0)
-
-// (hi, lo) FP32 pair of a value: hi = RN(v), lo = RN(v - hi)
-float2 split2(long double v) {
-  float hi = (float)v;
-  float lo = (float)(v - (long double)hi);
-  return make_float2(hi, lo);
-}
 
 // ---- basis (Gauss-Legendre, Lagrange, barycentric derivative) -----------------------
 
@@ -437,6 +392,62 @@ adg_status after_state_set(adg_solver* s) {
 }  // namespace
 
 namespace adg {
+FluxArgs stage_flux_args(const adg_solver* s, int m) {
+  FluxArgs fa = base_flux_args(const_cast<adg_solver*>(s));
+  const bool pe = s->flux != ADG_FLUX_SYNC && s->npe > 0;
+  const bool random = s->opt.delay_mode == ADG_DELAY_RANDOM;
+  fa.pe_mode = pe ? 1 : 0;
+  fa.random = random ? 1 : 0;
+  if (pe) {
+    const int kmax = random ? s->opt.random_delay_max : s->max_delay;
+    for (int kt = 0; kt <= kmax && kt < kMaxCoefDelay; ++kt) {
+      if (s->flux == ADG_FLUX_STD_DELAYED) {
+        fa.ctab[kt][0] = 1.0;
+        fa.ctabf[kt][0] = make_float2(1.0f, 0.0f);
+      } else {
+        long double c[kMaxN];
+        at_weights_ld(s->np, (long double)kt + s->rkc[m], c);
+        for (int l = 0; l <= s->np; ++l) {
+          fa.ctab[kt][l] = (double)c[l];
+          fa.ctabf[kt][l] = split2(c[l]);
+        }
+      }
+    }
+  }
+  return fa;
+}
+
+VolArgs stage_vol_args(const adg_solver* s, int m) {
+  VolArgs va;
+  std::memset(&va, 0, sizeof(va));
+  va.m = s->margs;
+  va.tab = s->tab_dev;
+  va.gamma = s->opt.gamma;
+  va.gammaf = split2(s->opt.gamma);
+  va.mode = s->rk2n ? kMode2N : kMode2R;
+  va.stage = m;
+  va.last = (m == s->stages - 1);
+  va.dt = s->dt;
+  if (s->rk2n) {
+    va.ca = s->rka[m];
+    va.cb = s->rkb[m];
+  } else {
+    va.ca = s->dt * s->rka[m];
+    va.cb = s->dt * s->rkb[m];
+  }
+  va.caf = split2(va.ca);
+  va.cbf = split2(va.cb);
+  va.dtf = split2(va.dt);
+  va.w_in = s->w;
+  va.r_in = s->x;
+  va.w = s->w;
+  va.x = s->x;
+  va.fl = s->fl;
+  va.tr = s->tr;
+  va.write_traces = 1;
+  return va;
+}
+
 // Helpers for adg_rhs_noalloc (noalloc.cu): the same operator tables without a handle,
 // and the per-thread error text that adg_last_error(NULL) returns.
 void noalloc_build_tables(int N, const double* h, OpTables* T) {
@@ -680,62 +691,20 @@ adg_status adg_step(adg_solver* s, int n_steps) {
     if (!random) caa_step(s->flux, s->max_delay, s->np, n, &comm, &k);
     const bool store_step = pe && (random || comm);
     for (int m = 0; m < s->stages; ++m) {
-      FluxArgs fa = base_flux_args(s);
-      fa.pe_mode = pe ? 1 : 0;
+      FluxArgs fa = stage_flux_args(s, m);
       if (pe) {
         if (store_step && m == 0) {
           s->head = (s->head + 1) % s->depth;
           fa.store = 1;
         }
         fa.head = s->head < 0 ? 0 : s->head;
-        fa.random = random ? 1 : 0;
         fa.uniform_delay = random ? 0 : (comm ? 0 : k);
         fa.step = n;
-        const int kmax = random ? s->opt.random_delay_max : (comm ? 0 : k);
-        for (int kt = 0; kt <= kmax && kt < kMaxCoefDelay; ++kt) {
-          if (s->flux == ADG_FLUX_STD_DELAYED) {
-            fa.ctab[kt][0] = 1.0;
-            fa.ctabf[kt][0] = make_float2(1.0f, 0.0f);
-          } else {
-            long double c[kMaxN];
-            at_weights_ld(s->np, (long double)kt + s->rkc[m], c);
-            for (int l = 0; l <= s->np; ++l) {
-              fa.ctab[kt][l] = (double)c[l];
-              fa.ctabf[kt][l] = split2(c[l]);
-            }
-          }
-        }
       }
       ADG_CUDA(s, prof_begin(s, 0));
       ADG_CUDA(s, launch_flux(s->prec, s->dim, s->N, fa, s->stream));
       ADG_CUDA(s, prof_end(s));
-      VolArgs va;
-      std::memset(&va, 0, sizeof(va));
-      va.m = s->margs;
-      va.tab = s->tab_dev;
-      va.gamma = s->opt.gamma;
-      va.gammaf = split2(s->opt.gamma);
-      va.mode = s->rk2n ? kMode2N : kMode2R;
-      va.stage = m;
-      va.last = (m == s->stages - 1);
-      va.dt = s->dt;
-      if (s->rk2n) {
-        va.ca = s->rka[m];
-        va.cb = s->rkb[m];
-      } else {
-        va.ca = s->dt * s->rka[m];
-        va.cb = s->dt * s->rkb[m];
-      }
-      va.caf = split2(va.ca);
-      va.cbf = split2(va.cb);
-      va.dtf = split2(va.dt);
-      va.w_in = s->w;
-      va.r_in = s->x;
-      va.w = s->w;
-      va.x = s->x;
-      va.fl = s->fl;
-      va.tr = s->tr;
-      va.write_traces = 1;
+      VolArgs va = stage_vol_args(s, m);
       ADG_CUDA(s, prof_begin(s, 1));
       ADG_CUDA(s, launch_vol(s->prec, s->dim, s->N, va, s->stream));
       ADG_CUDA(s, prof_end(s));

@@ -27,13 +27,13 @@ struct IPow { static constexpr int value = B * IPow<B, E - 1>::value; };
 template <int B>
 struct IPow<B, 0> { static constexpr int value = 1; };
 
-// Elements per block: about 128 threads per block, one thread per node.
-template <int D, int N>
+// Element tile of the volume kernel: about TT threads per block, one thread per node.
+template <int D, int N, int TT = 128>
 struct Tile {
   static constexpr int ND = IPow<N, D>::value;
   static constexpr int NF = ND / N;
   static constexpr int NV = D + 2;
-  static constexpr int EPB = (128 / ND) > 0 ? (128 / ND) : 1;
+  static constexpr int EPB = (TT / ND) > 0 ? (TT / ND) : 1;
   static constexpr int THREADS = EPB * ND;
 };
 
@@ -149,10 +149,10 @@ __device__ __forceinline__ int face_index(int d, const int* ix) {
 }
 
 // Traces of a tile of elements held in shared memory sX[el][v][node] -> tr.
-template <int D, int N, typename R>
+template <int D, int N, typename R, int TT = 128>
 __device__ __forceinline__ void write_traces(const MeshArgs& m, const OpTables* tab, const R* sX,
                                              int e0, typename Arith<R>::S* tr) {
-  using T = Tile<D, N>;
+  using T = Tile<D, N, TT>;
   constexpr int ND = T::ND, NF = T::NF, NV = T::NV, EPB = T::EPB;
   constexpr int TOTAL = EPB * 2 * D * NV * NF;
   const int ne = (int)m.ne;
@@ -261,15 +261,16 @@ struct Update<double> {
   }
 };
 
-template <int D, int N, typename R>
-__global__ void __launch_bounds__(Tile<D, N>::THREADS) vol_kernel(const VolArgs A) {
-  using T = Tile<D, N>;
+// One element tile (tile index `tile`) of the volume/update kernel.  A is read through a
+// reference so the batched kernels can pass per-instance arguments kept in device memory.
+template <int D, int N, typename R, int TT>
+__device__ __forceinline__ void vol_body(const VolArgs& A, int tile, unsigned char* smem_raw) {
+  using T = Tile<D, N, TT>;
   using S = typename Arith<R>::S;
   constexpr int ND = T::ND, NF = T::NF, NV = T::NV, EPB = T::EPB;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   R* sF = reinterpret_cast<R*>(smem_raw);  // [EPB][D][NV][ND]
   const int el = threadIdx.x / ND, node = threadIdx.x - el * ND;
-  const int e0 = blockIdx.x * EPB;
+  const int e0 = tile * EPB;
   const int ne = (int)A.m.ne;
   const int e = e0 + el;
   const bool active = e < ne;
@@ -347,8 +348,14 @@ __global__ void __launch_bounds__(Tile<D, N>::THREADS) vol_kernel(const VolArgs 
 #pragma unroll
     for (int v = 0; v < NV; ++v) sX[(el * NV + v) * ND + node] = xnext[v];
     __syncthreads();
-    write_traces<D, N, R>(A.m, A.tab, sX, e0, reinterpret_cast<S*>(A.tr));
+    write_traces<D, N, R, TT>(A.m, A.tab, sX, e0, reinterpret_cast<S*>(A.tr));
   }
+}
+
+template <int D, int N, typename R, int TT = 128>
+__global__ void __launch_bounds__(Tile<D, N, TT>::THREADS) vol_kernel(const VolArgs A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  vol_body<D, N, R, TT>(A, blockIdx.x, smem_raw);
 }
 
 // Random-delay draw (same definition as the host schedule).
@@ -359,15 +366,14 @@ __device__ __forceinline__ uint64_t splitmix64_dev(uint64_t x) {
   return z ^ (z >> 31);
 }
 
-// grid: x over (element, face node) of one direction, y = direction d
+// One block of face-flux threads: block bx over (element, face node) of direction d.
 template <int D, int N, typename R>
-__global__ void __launch_bounds__(256) flux_kernel(const FluxArgs A) {
+__device__ __forceinline__ void flux_body(const FluxArgs& A, int bx, int d) {
   using S = typename Arith<R>::S;
   constexpr int NF = IPow<N, D - 1>::value, NV = D + 2;
   const int ne = (int)A.m.ne;
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  const int g = bx * blockDim.x + threadIdx.x;
   if (g >= ne * NF) return;
-  const int d = blockIdx.y;
   const int e = g / NF;
   const int j = g - e * NF;
   int ec[3];
@@ -447,6 +453,12 @@ __global__ void __launch_bounds__(256) flux_kernel(const FluxArgs A) {
   S* fl = reinterpret_cast<S*>(A.fl);
 #pragma unroll
   for (int v = 0; v < NV; ++v) Arith<R>::store(fl + ((d * NV + v) * ne + e) * NF + j, f[v]);
+}
+
+// grid: x over (element, face node) of one direction, y = direction d
+template <int D, int N, typename R>
+__global__ void __launch_bounds__(256) flux_kernel(const FluxArgs A) {
+  flux_body<D, N, R>(A, blockIdx.x, blockIdx.y);
 }
 
 // ------------------------------------------------------------------------------------

@@ -1,0 +1,110 @@
+"""Batched solver (adg_batch_*): many uneven vortex instances in one CUDA-graph step.
+
+The batched kernels run the single-instance element code, so every instance must equal a
+separate solver handle bit for bit; one small instance is also checked against the oracle.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2603_28710_gb300 import adg
+from paper_2603_28710_gb300.inputs import vortex_instances
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2603_28710_gb300 import build
+    build.build()
+
+
+INSTANCES = [dict(n_elem=(16, 16), degree=2, P=(2, 2), max_delay=2, beta=5.0, x0=0.0, y0=0.0),
+             dict(n_elem=(24, 24), degree=3, P=(4, 3), max_delay=3, beta=3.0, x0=1.0, y0=-1.0),
+             dict(n_elem=(32, 16), degree=3, P=(2, 4), max_delay=4, beta=2.0, x0=-1.5, y0=0.5),
+             dict(n_elem=(8, 8), degree=4, P=(2, 2), max_delay=2, beta=4.0, x0=0.3, y0=0.2),
+             dict(n_elem=(20, 20), degree=5, P=(4, 4), max_delay=3, beta=1.5, x0=-0.5, y0=1.5),
+             dict(n_elem=(12, 12), degree=2, P=(3, 3), max_delay=4, beta=2.5, x0=2.0, y0=-2.0)]
+
+
+def singles_after(insts, steps, **kw):
+    out = []
+    for ins in insts:
+        s = adg.Solver(n_elem=ins["n_elem"], degree=ins["degree"], P=ins["P"],
+                       max_delay=ins["max_delay"], **kw)
+        s.init_vortex(beta=ins["beta"], x0=ins["x0"], y0=ins["y0"])
+        s.step(steps)
+        out.append(s.get_state())
+        s.close()
+    return out
+
+
+@pytest.mark.parametrize("precision", ["fp64", "df64", "fp32"])
+@pytest.mark.parametrize("flux,mode", [("at", "caa"), ("std", "caa"), ("at_trace", "random")])
+def test_batch_equals_separate_solvers_bitwise(precision, flux, mode):
+    kw = dict(flux=flux, rk="ck45", cfl=0.1, precision=precision, delay_mode=mode,
+              random_delay_max=2, seed=3)
+    b = adg.Batch(INSTANCES, **kw)
+    for i, ins in enumerate(INSTANCES):
+        b.init_vortex(i, beta=ins["beta"], x0=ins["x0"], y0=ins["y0"])
+    b.step(7)
+    b.step(4)
+    ref = singles_after(INSTANCES, 11, **kw)
+    for i in range(len(INSTANCES)):
+        assert b.info(i)["step"] == 11
+        assert np.array_equal(b.get_state(i), ref[i]), f"instance {i}"
+    b.close()
+
+
+def test_batch_after_autotune_and_reset():
+    kw = dict(flux="at", rk="rk33", cfl=0.1, precision="df64")
+    b = adg.Batch(INSTANCES, **kw)
+    tiles = b.autotune(trials=2)
+    assert len(tiles) == len({ins["degree"] for ins in INSTANCES})
+    assert all(t in (64, 128, 256) for t in tiles)
+    with pytest.raises(adg.AdgError):
+        b.step(1)                      # autotuning leaves no valid state
+    for i, ins in enumerate(INSTANCES):
+        b.init_vortex(i, beta=ins["beta"], x0=ins["x0"], y0=ins["y0"])
+    b.step(9)
+    ref = singles_after(INSTANCES, 9, **kw)
+    for i in range(len(INSTANCES)):
+        assert np.array_equal(b.get_state(i), ref[i]), f"instance {i}"
+
+
+def test_batch_instance_matches_oracle():
+    ins = INSTANCES[0]
+    b = adg.Batch([ins], flux="at", rk="ck45", dt=0.01, precision="df64")
+    b.init_vortex(0, beta=ins["beta"], x0=ins["x0"], y0=ins["y0"])
+    b.step(10)
+    o = O.Oracle(n_elem=ins["n_elem"], degree=ins["degree"], P=ins["P"],
+                 max_delay=ins["max_delay"], flux="at", rk="ck45", dt=0.01)
+    o.set_state(o.init_vortex(beta=ins["beta"], x0=ins["x0"], y0=ins["y0"]))
+    o.step(10)
+    u, uo = b.get_state(0), o.get_state()
+    assert np.linalg.norm(u - uo) / np.linalg.norm(uo) < 1e-12
+
+
+def test_sixty_four_uneven_vortex_instances():
+    # batched workload: 64 vortices, beta in [1,5], centres in [-2,2]^2, meshes 32^2..256^2,
+    # degrees 2..5, L in {2,3,4}; 8x8 subdomains; FP32 operator, FP64 accumulation
+    specs = vortex_instances(64, seed=7)
+    insts = [dict(n_elem=(s["n"], s["n"]), degree=s["degree"], P=(8, 8), max_delay=s["max_delay"])
+             for s in specs]
+    b = adg.Batch(insts, flux="at", rk="ck45", cfl=0.1, precision="fp32")
+    b.autotune(trials=2)
+    for i, s in enumerate(specs):
+        b.init_vortex(i, beta=s["beta"], x0=s["x0"], y0=s["y0"])
+    b.step(6)
+    for i in (0, 17, 63):
+        s = specs[i]
+        one = adg.Solver(n_elem=(s["n"], s["n"]), degree=s["degree"], P=(8, 8),
+                         max_delay=s["max_delay"], flux="at", rk="ck45", cfl=0.1, precision="fp32")
+        one.init_vortex(beta=s["beta"], x0=s["x0"], y0=s["y0"])
+        one.step(6)
+        assert np.array_equal(b.get_state(i), one.get_state())
+    for i in range(64):
+        assert np.isfinite(b.get_state(i)).all()
