@@ -58,7 +58,9 @@ typedef enum {
   ADG_FLUX_SYNC = 0,        /* Algorithm 1: every face uses current data; P ignored       */
   ADG_FLUX_STD_DELAYED = 1, /* Algorithm 2 / Eq. 13: reuse the stored flux of level n-k   */
   ADG_FLUX_AT = 2,          /* Algorithm 3 / Eq. 14: AT combination of stored fluxes      */
-  ADG_FLUX_AT_TRACE = 3     /* AT extrapolation of both stored traces, then Eq. 8         */
+  ADG_FLUX_AT_TRACE = 3,    /* AT extrapolation of both stored traces, then Eq. 8         */
+  ADG_FLUX_LEARNED = 4      /* as AT_TRACE, each extrapolated trace corrected by the learned
+                               predictor (adg_set_learned_model); needs at_np = 2       */
 } adg_flux;
 
 typedef enum {
@@ -252,6 +254,51 @@ adg_status adg_batch_l2_error_vortex(adg_batch* b, int i, double t, double beta,
 int adg_batch_num_groups(const adg_batch* b);
 const char* adg_batch_last_error(const adg_batch* b);
 void adg_batch_destroy(adg_batch* b);
+
+/* ---- learned ghost-trace predictor ------------------------------------------------- */
+/* A small MLP (4 -> 64 -> 64 -> 1, tanh hidden layers) with BF16 weights and FP32
+ * accumulation, used by ADG_FLUX_LEARNED to correct the AT extrapolation of subdomain
+ * traces.  Not part of the paper's method: an add-on whose error is judged against, and
+ * which falls back to, the plain AT extrapolation.  Parameters: adg_mlp_num_params()
+ * values laid out W1[64][4] | b1[64] | W2[64][64] | b2[64] | w3[64] | b3.
+ * All pointers below are DEVICE pointers; work is enqueued on cuda_stream. */
+int adg_mlp_num_params(void);
+/* Mean squared error over n samples (x[n][4], target[n]): ADDS d(loss)/d(params) to grad
+ * (FP32, one value per parameter) and the loss to *loss (one float). */
+adg_status adg_mlp_grad(const uint16_t* params_bf16, const float* x, const float* target,
+                        int64_t n, float* grad, float* loss, void* cuda_stream);
+/* y[n] = MLP(x[n][4]). */
+adg_status adg_mlp_forward(const uint16_t* params_bf16, const float* x, int64_t n, float* y,
+                           void* cuda_stream);
+/* One Adam step (step counter t >= 1) on FP32 master params with moments m, v; writes the
+ * BF16 copy and zeroes grad. */
+adg_status adg_mlp_adam(float* params, uint16_t* params_bf16, float* grad, float* m, float* v,
+                        float lr, float beta1, float beta2, float eps, int t, void* cuda_stream);
+/* BF16 copy (round to nearest even) of FP32 params. */
+adg_status adg_mlp_to_bf16(const float* params, uint16_t* params_bf16, void* cuda_stream);
+
+/* Model of ADG_FLUX_LEARNED: params_bf16 (HOST, adg_mlp_num_params() BF16 values) and the
+ * trust bound.  Per trace value the AT extrapolation E3 (three levels) and the linear one
+ * E2 (two levels) give the error estimate e = E3 - E2; the network output y is applied as
+ * E3 + e y only when |y| <= trust, so a correction never exceeds trust times AT's own
+ * error estimate; otherwise (and where e is at rounding level) E3 stands. */
+adg_status adg_set_learned_model(adg_solver* s, const uint16_t* params_bf16, float trust);
+/* Trace log for training data: while set, every RK stage of adg_step first appends one
+ * record with the traces of the current stage input on all subdomain faces (both sides),
+ * FP64, to the DEVICE buffer dev_log (capacity n_records records; later stages are not
+ * logged once it is full).  *record_len (nullable) = values per record
+ * = 2 (sides) x (dim+2) x n_subdomain_faces x (degree+1)^(dim-1), ordered
+ * [side][var][face][face node].  dev_log = NULL switches logging off. */
+adg_status adg_set_trace_log(adg_solver* s, double* dev_log, int64_t n_records,
+                             int64_t* record_len);
+/* Training samples from a trace log of a synchronous run (records step*stages + stage):
+ * dev_picks[n][4] = (channel within a record, step, stage, delay k >= 1) with
+ * step - k - 2 >= 0.  Writes the network inputs dev_x[n][4], the targets dev_target[n]
+ * (truth minus AT extrapolation, in units of the AT error estimate E3 - E2) and dev_ok[n]
+ * (0 where that estimate is at rounding level, below 1e-9 of the levels: no sample).  Uses the solver's RK stage offsets. */
+adg_status adg_learned_samples(adg_solver* s, const double* dev_log, int64_t n_records,
+                               const int32_t* dev_picks, int64_t n, float* dev_x,
+                               float* dev_target, int32_t* dev_ok);
 
 /* ---- host-only helpers (no GPU needed) ---------------------------------------------- */
 

@@ -16,7 +16,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libadg.so")
 
-FLUX = {"sync": 0, "std": 1, "at": 2, "at_trace": 3}
+FLUX = {"sync": 0, "std": 1, "at": 2, "at_trace": 3, "learned": 4}
 DELAY = {"caa": 0, "random": 1}
 RK = {"rk22": 0, "rk33": 1, "ck45": 2}
 PREC = {"fp64": 0, "fp32": 1, "df64": 2}
@@ -31,7 +31,9 @@ SYMBOLS = ["adg_default_options", "adg_create", "adg_set_state", "adg_init_vorte
            "adg_batch_create", "adg_batch_init_vortex", "adg_batch_set_state", "adg_batch_step",
            "adg_batch_autotune", "adg_batch_get_state", "adg_batch_info",
            "adg_batch_l2_error_vortex", "adg_batch_num_groups", "adg_batch_last_error",
-           "adg_batch_destroy", "adg_host_gauss", "adg_host_at_coeffs",
+           "adg_batch_destroy", "adg_mlp_num_params", "adg_mlp_grad", "adg_mlp_forward",
+           "adg_mlp_adam", "adg_mlp_to_bf16", "adg_set_learned_model", "adg_set_trace_log",
+           "adg_learned_samples", "adg_host_gauss", "adg_host_at_coeffs",
            "adg_host_rk", "adg_host_schedule", "adg_host_num_interfaces"]
 
 
@@ -100,6 +102,15 @@ def lib():
             "adg_batch_num_groups": ([P], I),
             "adg_batch_last_error": ([P], ctypes.c_char_p),
             "adg_batch_destroy": ([P], None),
+            "adg_mlp_num_params": ([], I),
+            "adg_mlp_grad": ([P, P, P, I64, P, P, P], I),
+            "adg_mlp_forward": ([P, P, I64, P, P], I),
+            "adg_mlp_adam": ([P, P, P, P, P, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                              ctypes.c_float, I, P], I),
+            "adg_mlp_to_bf16": ([P, P, P], I),
+            "adg_set_learned_model": ([P, P, ctypes.c_float], I),
+            "adg_set_trace_log": ([P, P, I64, P], I),
+            "adg_learned_samples": ([P, P, I64, P, I64, P, P, P], I),
             "adg_host_gauss": ([I, P, P], I),
             "adg_host_at_coeffs": ([I, D, P], I),
             "adg_host_rk": ([I, P, P, P, P], I),
@@ -334,6 +345,27 @@ class Solver:
         n = np.zeros(2, np.int64)
         self._chk(self._L.adg_get_profile(self._h, _np_ptr(ms), _np_ptr(n)))
         return {"flux": (float(ms[0]), int(n[0])), "vol": (float(ms[1]), int(n[1]))}
+
+    def set_learned_model(self, params_bf16, trust=1.0):
+        """params_bf16: numpy uint16 array of adg_mlp_num_params() BF16 values."""
+        a = np.ascontiguousarray(params_bf16, dtype=np.uint16)
+        if a.size != lib().adg_mlp_num_params():
+            raise ValueError("wrong number of parameters")
+        self._chk(self._L.adg_set_learned_model(self._h, _np_ptr(a), trust))
+
+    def set_trace_log(self, log_tensor=None, n_records=0):
+        """Log subdomain-face traces of every stage input into a CUDA float64 tensor."""
+        rl = ctypes.c_int64()
+        ptr = ctypes.c_void_p(log_tensor.data_ptr()) if log_tensor is not None else None
+        self._chk(self._L.adg_set_trace_log(self._h, ptr, n_records, ctypes.byref(rl)))
+        return rl.value
+
+    def learned_samples(self, log_tensor, n_records, picks, x, target, ok):
+        """picks: CUDA int32 [n][4]; x: CUDA float32 [n][4]; target: [n]; ok: int32 [n]."""
+        self._chk(self._L.adg_learned_samples(
+            self._h, ctypes.c_void_p(log_tensor.data_ptr()), n_records,
+            ctypes.c_void_p(picks.data_ptr()), picks.shape[0], ctypes.c_void_p(x.data_ptr()),
+            ctypes.c_void_p(target.data_ptr()), ctypes.c_void_p(ok.data_ptr())))
 
     def check_finite(self):
         st = self._L.adg_check_finite(self._h)

@@ -90,6 +90,39 @@ struct TraceArgs {
   void* tr;
 };
 
+// Learned correction of subdomain traces (learned.cu).
+struct LearnArgs {
+  MeshArgs m;
+  double gamma;
+  float2 gammaf;
+  const void* ring;         // trace ring [level][2][v][slot][j]
+  void* fl;                 // face fluxes to overwrite on subdomain faces
+  const int32_t* face_d;    // [slot] direction
+  const int32_t* face_e;    // [slot] low-side element
+  const int32_t* pe_iface;  // [slot] interface (random mode)
+  const uint16_t* mlp;      // BF16 parameters
+  float trust;              // largest accepted |correction| in units of the level spread
+  int64_t npe;
+  int depth, head, random, uniform_delay, n_iface, dmax;
+  uint64_t seed;
+  int64_t step;
+  double ctab[kMaxCoefDelay][kMaxN];
+  float2 ctabf[kMaxCoefDelay][kMaxN];
+  double km[kMaxCoefDelay];  // stage delay k_m = k + c_m of each delay k
+  // per-channel work buffers (channel = ((slot * NF + j) * 2 + side) * (dim+2) + var)
+  void* E;                  // AT extrapolation (operator storage type)
+  double* s;                // AT error estimate E3 - E2 (0: no correction)
+  float* x;                 // network inputs [4]
+  float* y;                 // network outputs
+};
+cudaError_t launch_learned(int prec, int dim, int N, const LearnArgs& a, cudaStream_t s);
+cudaError_t launch_samples(const double* log, int64_t rec_len, int stages, const int32_t* picks,
+                           int n, const double* ctab, const double* kmtab, int kmax, float* x,
+                           float* target, int* ok, cudaStream_t s);
+cudaError_t launch_log_traces(int prec, int dim, int N, const void* tr, const int32_t* face_d,
+                              const int32_t* face_e, const MeshArgs& m, int64_t npe, double* out,
+                              cudaStream_t s);
+
 // Launchers (one per arithmetic), implemented in the kernel translation units.
 // prec: 0 = FP64, 1 = FP32, 2 = FP32 pair.
 cudaError_t launch_trace(int prec, int dim, int N, const TraceArgs& a, cudaStream_t s);

@@ -273,6 +273,8 @@ adg_status adg_batch_create(int n, const adg_mesh* meshes, const int* degrees, c
   *out = nullptr;
   if (n < 1 || !meshes || !degrees || !P || !max_delay)
     return bfail(nullptr, ADG_ERR_INVALID, "need n >= 1 and non-NULL meshes, degrees, P, max_delay");
+  if (flux == ADG_FLUX_LEARNED)
+    return bfail(nullptr, ADG_ERR_UNSUPPORTED, "the learned flux is not available in batches");
   adg_options o;
   if (opt) o = *opt;
   else adg_default_options(&o);

@@ -15,6 +15,10 @@
 
 using namespace adg;
 
+namespace {
+constexpr size_t kMlpParamCount = 4545;  // parameters of the learned predictor (mlp.cuh)
+}
+
 namespace adg {
 // (hi, lo) FP32 pair of a value: hi = RN(v), lo = RN(v - hi)
 float2 split2(long double v) {
@@ -324,7 +328,8 @@ void free_all(adg_solver* s) {
   for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
   s->ev_pool.clear();
   void* ptrs[] = {s->w, s->x, s->tr, s->fl, s->ring, s->pe_slot, s->pe_iface, s->tab_dev,
-                  s->red_partial, s->red_out, s->flag, s->tmp_u, s->tmp_k};
+                  s->red_partial, s->red_out, s->flag, s->tmp_u, s->tmp_k, s->pe_face_d,
+                  s->pe_face_e, s->mlp, s->lw_E, s->lw_s, s->lw_x, s->lw_y};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
@@ -488,7 +493,7 @@ adg_status adg_create(const adg_mesh* mesh, int degree, const int P[3], int max_
   if (degree < 1 || degree > 7) return fail(nullptr, ADG_ERR_INVALID, "degree must be in 1..7");
   if (!valid_degree(mesh->dim, degree))
     return fail(nullptr, ADG_ERR_UNSUPPORTED, "3D is built for degree 1..5");
-  if ((int)flux < 0 || (int)flux > 3) return fail(nullptr, ADG_ERR_INVALID, "unknown flux");
+  if ((int)flux < 0 || (int)flux > 4) return fail(nullptr, ADG_ERR_INVALID, "unknown flux");
   adg_options o;
   if (opt) o = *opt;
   else adg_default_options(&o);
@@ -503,6 +508,8 @@ adg_status adg_create(const adg_mesh* mesh, int degree, const int P[3], int max_
     return fail(nullptr, ADG_ERR_INVALID, "random_delay_max must be in 0..15");
   const int np = o.at_np > 0 ? o.at_np : degree;
   if (np > 7) return fail(nullptr, ADG_ERR_INVALID, "at_np must be <= 7");
+  if (flux == ADG_FLUX_LEARNED && np != 2)
+    return fail(nullptr, ADG_ERR_INVALID, "the learned flux needs at_np = 2 (three stored levels)");
   if (flux != ADG_FLUX_SYNC && o.delay_mode == ADG_DELAY_CAA) {
     int lmin = (flux == ADG_FLUX_STD_DELAYED) ? 1 : 0;
     if (max_delay < lmin || max_delay > 15)
@@ -564,6 +571,7 @@ adg_status adg_create(const adg_mesh* mesh, int degree, const int P[3], int max_
   s->n_iface = num_interfaces(s->dim, s->P);
   int32_t* slot_h = nullptr;
   int32_t* iface_h = nullptr;
+  std::vector<int32_t> face_d_h, face_e_h;
   if (flux != ADG_FLUX_SYNC) {
     slot_h = new (std::nothrow) int32_t[(size_t)s->dim * ne];
     iface_h = new (std::nothrow) int32_t[(size_t)s->dim * ne + 1];
@@ -586,6 +594,8 @@ adg_status adg_create(const adg_mesh* mesh, int degree, const int P[3], int max_
           for (int dd = s->dim - 1; dd >= 0; --dd)
             sub = sub * s->P[dd] + c[dd] / (s->margs.n[dd] / s->P[dd]);
           iface_h[s->npe] = off + sub;
+          face_d_h.push_back(d);
+          face_e_h.push_back((int32_t)e);
           slot_h[(int64_t)d * ne + e] = (int32_t)s->npe++;
         } else {
           slot_h[(int64_t)d * ne + e] = -1;
@@ -619,8 +629,17 @@ adg_status adg_create(const adg_mesh* mesh, int degree, const int P[3], int max_
   if (flux != ADG_FLUX_SYNC) {
     alloc((void**)&s->pe_slot, (size_t)s->dim * ne * sizeof(int32_t));
     alloc((void**)&s->pe_iface, (size_t)(s->npe + 1) * sizeof(int32_t));
-    size_t ringn = (size_t)s->depth * (flux == ADG_FLUX_AT_TRACE ? 2 : 1) * s->NV * s->npe * s->NF;
+    size_t ringn = (size_t)s->depth * (flux >= ADG_FLUX_AT_TRACE ? 2 : 1) * s->NV * s->npe * s->NF;
     alloc(&s->ring, (ringn + 1) * sb);
+    alloc((void**)&s->pe_face_d, (size_t)(s->npe + 1) * sizeof(int32_t));
+    if (flux == ADG_FLUX_LEARNED) {
+      const size_t nch = (size_t)(s->npe + 1) * s->NF * 2 * s->NV;
+      alloc(&s->lw_E, nch * sb);
+      alloc((void**)&s->lw_s, nch * sizeof(double));
+      alloc((void**)&s->lw_x, nch * 4 * sizeof(float));
+      alloc((void**)&s->lw_y, nch * sizeof(float));
+    }
+    alloc((void**)&s->pe_face_e, (size_t)(s->npe + 1) * sizeof(int32_t));
   }
   // NULL selects the legacy default stream (handle 0), as in the CUDA runtime itself
   s->stream = (cudaStream_t)o.cuda_stream;
@@ -632,6 +651,12 @@ adg_status adg_create(const adg_mesh* mesh, int degree, const int P[3], int max_
                          cudaMemcpyHostToDevice, s->stream);
     if (ce == cudaSuccess && s->npe > 0)
       ce = cudaMemcpyAsync(s->pe_iface, iface_h, (size_t)s->npe * sizeof(int32_t),
+                           cudaMemcpyHostToDevice, s->stream);
+    if (ce == cudaSuccess && s->npe > 0)
+      ce = cudaMemcpyAsync(s->pe_face_d, face_d_h.data(), (size_t)s->npe * sizeof(int32_t),
+                           cudaMemcpyHostToDevice, s->stream);
+    if (ce == cudaSuccess && s->npe > 0)
+      ce = cudaMemcpyAsync(s->pe_face_e, face_e_h.data(), (size_t)s->npe * sizeof(int32_t),
                            cudaMemcpyHostToDevice, s->stream);
   }
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(s->stream);
@@ -678,6 +703,8 @@ adg_status adg_step(adg_solver* s, int n_steps) {
   if (!s) return fail(nullptr, ADG_ERR_INVALID, "handle is NULL");
   if (n_steps < 0) return fail(s, ADG_ERR_INVALID, "n_steps must be >= 0");
   if (!s->has_state) return fail(s, ADG_ERR_STATE, "no state: call adg_set_state first");
+  if (s->flux == ADG_FLUX_LEARNED && !s->mlp)
+    return fail(s, ADG_ERR_STATE, "learned flux without a model: call adg_set_learned_model");
   if (!s->traces_valid) {
     adg_status st = launch_traces_of(s, s->w);
     if (st != ADG_OK) return st;
@@ -691,6 +718,12 @@ adg_status adg_step(adg_solver* s, int n_steps) {
     if (!random) caa_step(s->flux, s->max_delay, s->np, n, &comm, &k);
     const bool store_step = pe && (random || comm);
     for (int m = 0; m < s->stages; ++m) {
+      if (s->log && s->log_count < s->log_cap && s->npe > 0) {
+        const int64_t rec = (int64_t)2 * s->NV * s->npe * s->NF;
+        ADG_CUDA(s, launch_log_traces(s->prec, s->dim, s->N, s->tr, s->pe_face_d, s->pe_face_e,
+                                      s->margs, s->npe, s->log + s->log_count * rec, s->stream));
+        s->log_count += 1;
+      }
       FluxArgs fa = stage_flux_args(s, m);
       if (pe) {
         if (store_step && m == 0) {
@@ -704,6 +737,37 @@ adg_status adg_step(adg_solver* s, int n_steps) {
       ADG_CUDA(s, prof_begin(s, 0));
       ADG_CUDA(s, launch_flux(s->prec, s->dim, s->N, fa, s->stream));
       ADG_CUDA(s, prof_end(s));
+      if (s->flux == ADG_FLUX_LEARNED && pe && (random || !comm)) {
+        LearnArgs la;
+        std::memset(&la, 0, sizeof(la));
+        la.m = s->margs;
+        la.gamma = s->opt.gamma;
+        la.gammaf = split2(s->opt.gamma);
+        la.ring = s->ring;
+        la.fl = s->fl;
+        la.face_d = s->pe_face_d;
+        la.face_e = s->pe_face_e;
+        la.pe_iface = s->pe_iface;
+        la.mlp = s->mlp;
+        la.trust = s->trust;
+        la.npe = s->npe;
+        la.depth = s->depth;
+        la.head = fa.head;
+        la.random = fa.random;
+        la.uniform_delay = fa.uniform_delay;
+        la.n_iface = s->n_iface;
+        la.dmax = s->opt.random_delay_max;
+        la.seed = s->opt.seed;
+        la.step = n;
+        std::memcpy(la.ctab, fa.ctab, sizeof(la.ctab));
+        std::memcpy(la.ctabf, fa.ctabf, sizeof(la.ctabf));
+        for (int kt = 0; kt < kMaxCoefDelay; ++kt) la.km[kt] = kt + s->rkc[m];
+        la.E = s->lw_E;
+        la.s = s->lw_s;
+        la.x = s->lw_x;
+        la.y = s->lw_y;
+        ADG_CUDA(s, launch_learned(s->prec, s->dim, s->N, la, s->stream));
+      }
       VolArgs va = stage_vol_args(s, m);
       ADG_CUDA(s, prof_begin(s, 1));
       ADG_CUDA(s, launch_vol(s->prec, s->dim, s->N, va, s->stream));
@@ -814,6 +878,58 @@ adg_status adg_check_finite(adg_solver* s) {
   ADG_CUDA(s, cudaMemcpyAsync(&f, s->flag, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
   ADG_CUDA(s, cudaStreamSynchronize(s->stream));
   if (f) return fail(s, ADG_ERR_NONFINITE, "state holds NaN or Inf");
+  return ADG_OK;
+}
+
+adg_status adg_set_learned_model(adg_solver* s, const uint16_t* params_bf16, float trust) {
+  if (!s) return fail(nullptr, ADG_ERR_INVALID, "handle is NULL");
+  if (!params_bf16 || !(trust >= 0.0f)) return fail(s, ADG_ERR_INVALID, "bad model arguments");
+  if (!s->mlp) ADG_CUDA(s, cudaMalloc((void**)&s->mlp, kMlpParamCount * sizeof(uint16_t)));
+  ADG_CUDA(s, cudaMemcpyAsync(s->mlp, params_bf16, kMlpParamCount * sizeof(uint16_t),
+                              cudaMemcpyHostToDevice, s->stream));
+  ADG_CUDA(s, cudaStreamSynchronize(s->stream));
+  s->trust = trust;
+  return ADG_OK;
+}
+
+adg_status adg_set_trace_log(adg_solver* s, double* dev_log, int64_t n_records, int64_t* record_len) {
+  if (!s) return fail(nullptr, ADG_ERR_INVALID, "handle is NULL");
+  if (record_len) *record_len = (int64_t)2 * s->NV * s->npe * s->NF;
+  if (n_records < 0) return fail(s, ADG_ERR_INVALID, "n_records must be >= 0");
+  s->log = dev_log;
+  s->log_cap = dev_log ? n_records : 0;
+  s->log_count = 0;
+  return ADG_OK;
+}
+
+adg_status adg_learned_samples(adg_solver* s, const double* dev_log, int64_t n_records,
+                               const int32_t* dev_picks, int64_t n, float* dev_x,
+                               float* dev_target, int32_t* dev_ok) {
+  if (!s) return fail(nullptr, ADG_ERR_INVALID, "handle is NULL");
+  if (!dev_log || !dev_picks || !dev_x || !dev_target || !dev_ok || n < 0 || n >= (1ll << 31))
+    return fail(s, ADG_ERR_INVALID, "bad sample arguments");
+  (void)n_records;
+  // AT weights (N_p = 2) and stage delays for k = 0..15 and every stage
+  const int K = kMaxCoefDelay, S = s->stages;
+  std::vector<double> ctab((size_t)K * S * 3), km((size_t)K * S);
+  for (int k = 0; k < K; ++k)
+    for (int m = 0; m < S; ++m) {
+      long double c[kMaxN];
+      at_weights_ld(2, (long double)k + s->rkc[m], c);
+      for (int l = 0; l < 3; ++l) ctab[((size_t)k * S + m) * 3 + l] = (double)c[l];
+      km[(size_t)k * S + m] = k + s->rkc[m];
+    }
+  double* dtab = nullptr;
+  ADG_CUDA(s, cudaMalloc((void**)&dtab, (ctab.size() + km.size()) * sizeof(double)));
+  cudaError_t e = cudaMemcpy(dtab, ctab.data(), ctab.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(dtab + ctab.size(), km.data(), km.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = launch_samples(dev_log, (int64_t)2 * s->NV * s->npe * s->NF, S, dev_picks, (int)n, dtab,
+                       dtab + ctab.size(), K - 1, dev_x, dev_target, dev_ok, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  cudaFree(dtab);
+  if (e != cudaSuccess) return cuda_fail(s, e, "adg_learned_samples");
   return ADG_OK;
 }
 

@@ -392,7 +392,7 @@ __device__ __forceinline__ void flux_body(const FluxArgs& A, int bx, int d) {
     llf_flux<D, R>(wm, wp, d, gamma, f);
   } else {
     S* ring = reinterpret_cast<S*>(A.ring);
-    const bool traces = (A.flux_kind == 3);
+    const bool traces = (A.flux_kind >= 3);  // AT on traces, and the learned mode
     const int npe = (int)A.npe;
     const int lvl_stride = (traces ? 2 : 1) * NV * npe * NF;
     int kt = A.uniform_delay;

@@ -50,6 +50,17 @@ struct adg_solver {
   int64_t step = 0;
   double t = 0.0, dt = 0.0;
   std::string err;
+  // learned ghost-trace predictor and trace logging
+  int32_t* pe_face_d = nullptr;   // [slot] direction of the PE face
+  int32_t* pe_face_e = nullptr;   // [slot] element on its low side
+  uint16_t* mlp = nullptr;        // BF16 parameters (device)
+  void* lw_E = nullptr;           // learned-mode per-channel work buffers
+  double* lw_s = nullptr;
+  float* lw_x = nullptr;
+  float* lw_y = nullptr;
+  float trust = 1.0f;
+  double* log = nullptr;          // caller's device buffer of PE-face trace records
+  int64_t log_cap = 0, log_count = 0;
   // kernel timing (adg_set_profiling)
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;

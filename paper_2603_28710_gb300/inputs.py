@@ -35,3 +35,11 @@ def vortex_instances(count: int = 64, seed: int = 7):
                         n=int(rng.choice([32, 64, 128, 256])), degree=int(rng.integers(2, 6)),
                         max_delay=int(rng.integers(2, 5))))
     return out
+
+
+def vortex_params(count: int = 200, seed: int = 11):
+    """(beta, centre) sets for the training runs of the learned predictor: beta ~ U[1, 5],
+    centre ~ U([-2, 2]^2)."""
+    rng = np.random.default_rng(seed)
+    return [dict(beta=float(rng.uniform(1.0, 5.0)), x0=float(rng.uniform(-2.0, 2.0)),
+                 y0=float(rng.uniform(-2.0, 2.0))) for _ in range(count)]
