@@ -308,6 +308,39 @@ def batched_run(adg, stream, k=6):
             "autotune_s": tune_s}
 
 
+def tgv_run(adg, stream, k=3):
+    """3D Taylor-Green vortex, 64^3 hexes, p = 3, 8x8x8 subdomains, L = 4, AT flux,
+    CK4(5), CFL 0.1: throughput per operator arithmetic (one benchmark step = one schedule
+    cycle of L + N_p + 1 = 8 time steps)."""
+    import torch
+    out = {}
+    ndof = 5 * 64 ** 3 * 4 ** 3
+    for prec in ("fp64", "df64", "fp32"):
+        s = adg.Solver(dim=3, n_elem=(64, 64, 64), degree=3, lo=(0, 0, 0), hi=(2 * np.pi,) * 3,
+                       P=(8, 8, 8), max_delay=4, flux="at", rk="ck45", cfl=0.1, precision=prec,
+                       stream=stream.cuda_stream)
+        s.init_tgv(0.1)
+        s.step(8)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(8 * k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        s.set_profiling(True)
+        s.step(8)
+        prof = s.get_profile()
+        s.close()
+        out[prec] = {"value": ndof * 5 * 8 * k / (ms * 1e-3) / 1e9,
+                     "vol_ms_per_launch": prof["vol"][0] / max(prof["vol"][1], 1),
+                     "flux_ms_per_launch": prof["flux"][0] / max(prof["flux"][1], 1)}
+    out["workload"] = ("3D Taylor-Green vortex 64^3 hexes p=3 (83.9M DoF), 8x8x8 subdomains, "
+                       "CAA L=4, AT flux, CK4(5), CFL 0.1")
+    out["unit"] = METRIC
+    return out
+
+
 # ---- GPU arm -----------------------------------------------------------------------------
 def run_gpu(args, rank, world, local_rank):
     import torch
@@ -433,6 +466,9 @@ def run_gpu(args, rank, world, local_rank):
     batched = None
     if world == 1 and not args.no_batch:
         batched = batched_run(adg, stream)
+    tgv = None
+    if world == 1 and not args.no_3d:
+        tgv = tgv_run(adg, stream)
 
     clocks = clk.summary()
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
@@ -448,7 +484,7 @@ def run_gpu(args, rank, world, local_rank):
             "kernels": {"vol_kernel": {"ms_per_launch": vol_ms / max(vol_n, 1), "launches": vol_n},
                         "flux_kernel": {"ms_per_launch": flux_ms / max(flux_n, 1),
                                         "launches": flux_n}},
-            "variants": variants, "batched": batched}
+            "variants": variants, "batched": batched, "taylor_green_3d": tgv}
     print(json.dumps(line), flush=True)
 
 
@@ -465,6 +501,7 @@ def main():
                     help="skip the FP64 / FP32-pair / FP32 comparison runs")
     ap.add_argument("--variant-steps", type=int, default=10)
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-instances run")
+    ap.add_argument("--no-3d", action="store_true", help="skip the 3D Taylor-Green runs")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -28,6 +28,14 @@ struct OpTables {
   float2 Lmf[3][kMaxN];
   float2 Tpf[kMaxN];
   float2 Tmf[kMaxN];
+  // the operator tables times the time step (2N scheme: the volume kernel then produces
+  // dt * k directly); filled once dt is known
+  double Qs[3][kMaxN * kMaxN];
+  double Lps[3][kMaxN];
+  double Lms[3][kMaxN];
+  float2 Qsf[3][kMaxN * kMaxN];
+  float2 Lpsf[3][kMaxN];
+  float2 Lmsf[3][kMaxN];
 };
 
 struct MeshArgs {
@@ -56,6 +64,7 @@ struct __align__(16) VolArgs {
   const void* fl;        // face fluxes [d][v][e][j] (storage type of the arithmetic)
   void* tr;              // traces of the next stage input [d][side][v][e][j]
   int write_traces;
+  int scaled;            // 1: use the dt-scaled tables (2N), the accumulator is dt * k
 };
 
 struct __align__(16) FluxArgs {

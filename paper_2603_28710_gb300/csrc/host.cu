@@ -388,6 +388,20 @@ adg_status after_state_set(adg_solver* s) {
     if (s->opt.t_end > 0) dt = s->opt.t_end / std::ceil(s->opt.t_end / dt);
     s->dt = dt;
   }
+  // dt-scaled operator tables for the 2N update
+  for (int d = 0; d < 3; ++d) {
+    for (int i = 0; i < s->N * s->N; ++i) {
+      s->tab.Qs[d][i] = s->tab.Q[d][i] * s->dt;
+      s->tab.Qsf[d][i] = split2((long double)s->tab.Q[d][i] * s->dt);
+    }
+    for (int i = 0; i < s->N; ++i) {
+      s->tab.Lps[d][i] = s->tab.Lp[d][i] * s->dt;
+      s->tab.Lms[d][i] = s->tab.Lm[d][i] * s->dt;
+      s->tab.Lpsf[d][i] = split2((long double)s->tab.Lp[d][i] * s->dt);
+      s->tab.Lmsf[d][i] = split2((long double)s->tab.Lm[d][i] * s->dt);
+    }
+  }
+  ADG_CUDA(s, cudaMemcpyAsync(s->tab_dev, &s->tab, sizeof(OpTables), cudaMemcpyHostToDevice, s->stream));
   adg_status st = launch_traces_of(s, s->w);
   if (st != ADG_OK) return st;
   s->traces_valid = true;
@@ -450,6 +464,7 @@ VolArgs stage_vol_args(const adg_solver* s, int m) {
   va.fl = s->fl;
   va.tr = s->tr;
   va.write_traces = 1;
+  va.scaled = s->rk2n ? 1 : 0;
   return va;
 }
 

@@ -226,8 +226,8 @@ struct Update {
       return r1;
     }
     const R cA = Arith<R>::pair(A.ca, A.caf), cB = Arith<R>::pair(A.cb, A.cbf);
-    const R dt = Arith<R>::pair(A.dt, A.dtf);
-    const R q1 = (A.stage > 0) ? r_fma(cA, Arith<R>::load(x + idx), dt * k) : dt * k;
+    const R dtk = A.scaled ? k : Arith<R>::pair(A.dt, A.dtf) * k;
+    const R q1 = (A.stage > 0) ? r_fma(cA, Arith<R>::load(x + idx), dtk) : dtk;
     const double w1 = add_increment(w0, cB * q1);
     A.w[idx] = w1;
     if (!A.last) Arith<R>::store(x + idx, q1);
@@ -252,8 +252,8 @@ struct Update<double> {
       x[idx] = r1;
       return r1;
     }
-    const double q0 = A.stage > 0 ? x[idx] : 0.0;
-    const double q1 = fma(A.ca, q0, A.dt * k);
+    const double dtk = A.scaled ? k : A.dt * k;
+    const double q1 = A.stage > 0 ? fma(A.ca, x[idx], dtk) : dtk;
     const double w1 = fma(A.cb, q1, w0);
     A.w[idx] = w1;
     if (!A.last) x[idx] = q1;
@@ -311,7 +311,8 @@ __device__ __forceinline__ void vol_body(const VolArgs& A, int tile, unsigned ch
       const int base = node - ix[d] * stride;
 #pragma unroll
       for (int a = 0; a < N; ++a) {
-        const R q = Arith<R>::tab(A.tab->Q[d], A.tab->Qf[d], ix[d] * N + a);
+        const R q = A.scaled ? Arith<R>::tab(A.tab->Qs[d], A.tab->Qsf[d], ix[d] * N + a)
+                             : Arith<R>::tab(A.tab->Q[d], A.tab->Qf[d], ix[d] * N + a);
 #pragma unroll
         for (int v = 0; v < NV; ++v)
           acc[v] = acc_fma(q, sF[((el * D + d) * NV + v) * ND + base + a * stride], acc[v]);
@@ -321,8 +322,10 @@ __device__ __forceinline__ void vol_body(const VolArgs& A, int tile, unsigned ch
     for (int d = 0; d < D; ++d) {
       const int j = face_index<D, N>(d, ix);
       const int elo = elem_shift(A.m, e, ec, d, -1);
-      const R lp = Arith<R>::tab(A.tab->Lp[d], A.tab->Lpf[d], ix[d]);
-      const R lm = Arith<R>::tab(A.tab->Lm[d], A.tab->Lmf[d], ix[d]);
+      const R lp = A.scaled ? Arith<R>::tab(A.tab->Lps[d], A.tab->Lpsf[d], ix[d])
+                            : Arith<R>::tab(A.tab->Lp[d], A.tab->Lpf[d], ix[d]);
+      const R lm = A.scaled ? Arith<R>::tab(A.tab->Lms[d], A.tab->Lmsf[d], ix[d])
+                            : Arith<R>::tab(A.tab->Lm[d], A.tab->Lmf[d], ix[d]);
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         const R fhi = Arith<R>::load(fl + ((d * NV + v) * ne + e) * NF + j);
