@@ -99,6 +99,11 @@ __device__ __forceinline__ float r_max(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ double r_fma(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float r_fma(float a, float b, float c) { return fmaf(a, b, c); }
 
+// exact halving
+__device__ __forceinline__ double half(double x) { return 0.5 * x; }
+__device__ __forceinline__ float half(float x) { return 0.5f * x; }
+__device__ __forceinline__ df64 half(df64 x) { return df64(0.5f * x.hi, 0.5f * x.lo); }
+
 // accumulators: plain FMA chains for the native types
 __device__ __forceinline__ double acc_zero(double) { return 0.0; }
 __device__ __forceinline__ float acc_zero(float) { return 0.0f; }

@@ -57,13 +57,14 @@ template <int D, typename R>
 __device__ __forceinline__ void euler_flux_all(const R (&w)[D + 2], R gm1, R (&F)[D][D + 2]) {
   const R irho = r_rcp(w[0]);
   R u[D];
-  R kin2 = R(0.0f);
+  typename Arith<R>::Acc kacc = acc_zero(typename Arith<R>::Acc());
 #pragma unroll
   for (int d = 0; d < D; ++d) {
     u[d] = w[1 + d] * irho;
-    kin2 = r_fma(w[1 + d], u[d], kin2);
+    kacc = acc_fma(w[1 + d], u[d], kacc);
   }
-  const R p = gm1 * (w[D + 1] - R(0.5f) * kin2);
+  const R kin2 = acc_result(kacc);
+  const R p = gm1 * (w[D + 1] - half(kin2));
   const R ep = w[D + 1] + p;
 #pragma unroll
   for (int d = 0; d < D; ++d) {
@@ -148,9 +149,23 @@ __device__ __forceinline__ int face_index(int d, const int* ix) {
   return j;
 }
 
-// Traces of a tile of elements held in shared memory sX[el][v][node] -> tr.
-template <int D, int N, typename R, int TT = 128>
-__device__ __forceinline__ void write_traces(const MeshArgs& m, const OpTables* tab, const R* sX,
+// Arithmetic of the trace interpolation for an operator arithmetic R: the FP32-pair kernels
+// interpolate in native FP64 (their FP64 pipe is otherwise idle and the RK update hands
+// over the FP64 stage input), the others in R itself.
+template <typename R> struct TraceCompute { using C = R; };
+template <> struct TraceCompute<df64> { using C = double; };
+
+__device__ __forceinline__ void store_trace(double* p, double v) { *p = v; }
+__device__ __forceinline__ void store_trace(float* p, float v) { *p = v; }
+__device__ __forceinline__ void store_trace(float2* p, double v) {
+  const df64 q = d2df_int(v);
+  *p = make_float2(q.hi, q.lo);
+}
+__device__ __forceinline__ void store_trace(float2* p, df64 v) { *p = make_float2(v.hi, v.lo); }
+
+// Traces of a tile of elements held in shared memory sX[el][v][node] (compute type C) -> tr.
+template <int D, int N, typename R, int TT = 128, typename C = R>
+__device__ __forceinline__ void write_traces(const MeshArgs& m, const OpTables* tab, const C* sX,
                                              int e0, typename Arith<R>::S* tr) {
   using T = Tile<D, N, TT>;
   constexpr int ND = T::ND, NF = T::NF, NV = T::NV, EPB = T::EPB;
@@ -168,20 +183,21 @@ __device__ __forceinline__ void write_traces(const MeshArgs& m, const OpTables* 
     const int stride = d == 0 ? 1 : (d == 1 ? N : N * N);
     const double* tw = side ? tab->Tp : tab->Tm;
     const float2* twf = side ? tab->Tpf : tab->Tmf;
-    typename Arith<R>::Acc acc = acc_zero(typename Arith<R>::Acc());
+    typename Arith<C>::Acc acc = acc_zero(typename Arith<C>::Acc());
 #pragma unroll
     for (int a = 0; a < N; ++a)
-      acc = acc_fma(Arith<R>::tab(tw, twf, a), sX[(el * NV + v) * ND + base + a * stride], acc);
-    Arith<R>::store(tr + ((ds * NV + v) * ne + e) * NF + j, acc_result(acc));
+      acc = acc_fma(Arith<C>::tab(tw, twf, a), sX[(el * NV + v) * ND + base + a * stride], acc);
+    store_trace(tr + ((ds * NV + v) * ne + e) * NF + j, acc_result(acc));
   }
 }
 
 template <int D, int N, typename R>
 __global__ void __launch_bounds__(Tile<D, N>::THREADS) trace_kernel(const TraceArgs A) {
   using T = Tile<D, N>;
+  using C = typename TraceCompute<R>::C;
   constexpr int ND = T::ND, NV = T::NV, EPB = T::EPB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  R* sX = reinterpret_cast<R*>(smem_raw);
+  C* sX = reinterpret_cast<C*>(smem_raw);
   const int el = threadIdx.x / ND, node = threadIdx.x - el * ND;
   const int e0 = blockIdx.x * EPB;
   const int e = e0 + el;
@@ -189,10 +205,10 @@ __global__ void __launch_bounds__(Tile<D, N>::THREADS) trace_kernel(const TraceA
   if (e < ne) {
 #pragma unroll
     for (int v = 0; v < NV; ++v)
-      sX[(el * NV + v) * ND + node] = Arith<R>::from_double(A.u[(v * ne + e) * ND + node]);
+      sX[(el * NV + v) * ND + node] = Arith<C>::from_double(A.u[(v * ne + e) * ND + node]);
   }
   __syncthreads();
-  write_traces<D, N, R>(A.m, A.tab, sX, e0, reinterpret_cast<typename Arith<R>::S*>(A.tr));
+  write_traces<D, N, R, 128, C>(A.m, A.tab, sX, e0, reinterpret_cast<typename Arith<R>::S*>(A.tr));
 }
 
 // ---- Runge-Kutta update of one node -------------------------------------------------
@@ -204,13 +220,22 @@ __device__ __forceinline__ double add_increment(double w0, df64 d) {
   return (w0 + f2d_int(d.hi)) + f2d_int(d.lo);
 }
 
+// Value of the next stage input handed to the trace interpolation (compute type C): the
+// operator's own value, or the FP64 one for the FP32-pair kernels.
+template <typename C, typename R>
+__device__ __forceinline__ C trace_value(double, R xr) { return xr; }
+template <>
+__device__ __forceinline__ double trace_value<double, df64>(double xd, df64) { return xd; }
+
 template <typename R>
 struct Update {
   using S = typename Arith<R>::S;
-  // returns the next stage input at this node/variable
-  __device__ static __forceinline__ R apply(const VolArgs& A, int idx, R k, R u_in) {
+  // returns the next stage input at this node/variable; xd receives it in FP64 where the
+  // update has it in FP64 (the FP32-pair traces use it)
+  __device__ static __forceinline__ R apply(const VolArgs& A, int idx, R k, R u_in, double& xd) {
     if (A.mode == kModeRHS) {
       A.kout[idx] = Arith<R>::to_double(k);
+      xd = Arith<R>::to_double(u_in);
       return u_in;
     }
     const double w0 = A.w[idx];
@@ -219,10 +244,14 @@ struct Update {
       const R cb = Arith<R>::pair(A.cb, A.cbf), ca = Arith<R>::pair(A.ca, A.caf);
       const double w1 = add_increment(w0, cb * k);
       A.w[idx] = w1;
-      if (A.last) return Arith<R>::from_double(w1);
-      const R w0r = (A.stage == 0) ? u_in : Arith<R>::from_double(w0);
-      const R r1 = r_fma(ca, k, w0r);
+      if (A.last) {
+        xd = w1;
+        return Arith<R>::from_double(w1);
+      }
+      const double r1d = add_increment(w0, ca * k);
+      const R r1 = Arith<R>::from_double(r1d);
       Arith<R>::store(x + idx, r1);
+      xd = r1d;
       return r1;
     }
     const R cA = Arith<R>::pair(A.ca, A.caf), cB = Arith<R>::pair(A.cb, A.cbf);
@@ -231,13 +260,16 @@ struct Update {
     const double w1 = add_increment(w0, cB * q1);
     A.w[idx] = w1;
     if (!A.last) Arith<R>::store(x + idx, q1);
+    xd = w1;
     return Arith<R>::from_double(w1);
   }
 };
 
 template <>
 struct Update<double> {
-  __device__ static __forceinline__ double apply(const VolArgs& A, int idx, double k, double u_in) {
+  __device__ static __forceinline__ double apply(const VolArgs& A, int idx, double k, double u_in,
+                                                 double& xd) {
+    xd = 0.0;
     if (A.mode == kModeRHS) {
       A.kout[idx] = k;
       return u_in;
@@ -337,21 +369,24 @@ __device__ __forceinline__ void vol_body(const VolArgs& A, int tile, unsigned ch
   }
 
   // 3. Runge-Kutta update; xnext = input of the next stage
-  R xnext[NV];
+  using C = typename TraceCompute<R>::C;
+  C xnext[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     const int idx = (v * ne + e) * ND + node;
-    xnext[v] = active ? Update<R>::apply(A, idx, acc_result(acc[v]), u[v]) : R(0.0f);
+    double xd = 0.0;
+    const R xr = active ? Update<R>::apply(A, idx, acc_result(acc[v]), u[v], xd) : R(0.0f);
+    xnext[v] = trace_value<C, R>(xd, xr);
   }
 
   // 4. traces of the next stage input
   if (A.write_traces) {
     __syncthreads();
-    R* sX = sF;  // reuse: [EPB][NV][ND]
+    C* sX = reinterpret_cast<C*>(smem_raw);  // reuse: [EPB][NV][ND]
 #pragma unroll
     for (int v = 0; v < NV; ++v) sX[(el * NV + v) * ND + node] = xnext[v];
     __syncthreads();
-    write_traces<D, N, R, TT>(A.m, A.tab, sX, e0, reinterpret_cast<S*>(A.tr));
+    write_traces<D, N, R, TT, C>(A.m, A.tab, sX, e0, reinterpret_cast<S*>(A.tr));
   }
 }
 
