@@ -241,10 +241,11 @@ adg_status adg_batch_set_state(adg_batch* b, int i, const double* u, int64_t cou
 /* Advances every instance by n_steps steps (graph replays; enqueued, does not wait).
  * Errors: ADG_ERR_STATE if an instance has no state. */
 adg_status adg_batch_step(adg_batch* b, int n_steps);
-/* Autotuner: for every degree group, times the volume launch with tiles of about 64, 128
- * and 256 threads on the real buffers and keeps the fastest; tile_threads (nullable)
- * receives one choice per group in increasing degree.  It overwrites every instance's
- * state (set states afterwards). */
+/* Autotuner: for every degree group, times on the real buffers the volume launch with
+ * tiles of about 64, 128 and 256 threads, each launched as one resident wave of persistent
+ * blocks and as one block per tile, and the face-flux launch in both shapes, and keeps the
+ * fastest; tile_threads (nullable) receives the tile chosen per group in increasing
+ * degree.  It overwrites every instance's state (set states afterwards). */
 adg_status adg_batch_autotune(adg_batch* b, int trials, int* tile_threads);
 adg_status adg_batch_get_state(adg_batch* b, int i, double* u, int64_t count, int on_device);
 adg_status adg_batch_info(const adg_batch* b, int i, double* t, int64_t* step, double* dt,

@@ -27,11 +27,24 @@ struct BatchGroupArgs {
   int total;         // virtual blocks in total
 };
 
-__device__ __forceinline__ int find_instance(const BatchGroupArgs& g, int vb) {
-  int lo = 0, hi = g.n - 1;
+// Instances whose block offsets a persistent block keeps in shared memory; larger groups
+// search the offsets in global memory.
+constexpr int kMaxSharedOffsets = 512;
+
+// Copy of the group's block offsets into shared memory (when they fit), once per block.
+__device__ __forceinline__ const int* stage_offsets(const BatchGroupArgs& g, int* soff) {
+  if (g.n >= kMaxSharedOffsets) return g.off;
+  for (int i = threadIdx.x; i <= g.n; i += blockDim.x) soff[i] = g.off[i];
+  __syncthreads();
+  return soff;
+}
+
+// instance k of virtual block vb: off[k] <= vb < off[k+1] (binary search)
+__device__ __forceinline__ int find_instance(const int* off, int n, int vb) {
+  int lo = 0, hi = n - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    if (g.off[mid] <= vb) lo = mid;
+    if (off[mid] <= vb) lo = mid;
     else hi = mid - 1;
   }
   return lo;
@@ -48,17 +61,45 @@ __device__ __forceinline__ void stage_args(T* dst, const T* src) {
   for (int i = threadIdx.x; i < (int)(sizeof(T) / 16); i += blockDim.x) d[i] = s[i];
 }
 
+// Register budget of the batched volume kernels.  The persistent loop and the arguments
+// read from shared memory raise their register use over the single-instance kernels (FP32:
+// 48 against 32 at 128 threads, over 90 for tiles of 64 threads), which cuts the occupancy
+// the latency-bound FP32 form needs.  Caps without spills (ptxas, sm_103a): 40 registers
+// in 2D, 48 at N = 4 and 8 and for tiles of at most 64 threads; 3D stays uncapped (40
+// spills at N = 6).
+template <int D, int N, typename R> struct VolRegs { static constexpr int value = 0; };
+template <int D, int N> struct VolRegs<D, N, float> {
+  static constexpr int value = D != 2 ? 0 : ((N == 4 || N == 8) ? 48 : 40);
+};
+
+// blocks per SM that leave `regs` registers per thread: each of the 4 SM sub-partitions
+// holds 16384 registers and a whole number of warps
+constexpr int min_blocks_for(int regs, int threads) {
+  if (regs == 0) return 1;
+  if (threads <= 64 && regs < 48) regs = 48;
+  const int warps = (threads + 31) / 32;
+  const int b = (16384 / (regs * 32)) * 4 / warps;
+  return b < 1 ? 1 : (b > 32 ? 32 : b);
+}
+
 template <int D, int N, typename R, int TT>
-__global__ void __launch_bounds__(Tile<D, N, TT>::THREADS)
+__global__ void __launch_bounds__(Tile<D, N, TT>::THREADS,
+                                  min_blocks_for(VolRegs<D, N, R>::value, Tile<D, N, TT>::THREADS))
 batch_vol_kernel(const VolArgs* va, int nstages, int stage, BatchGroupArgs g) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(16) VolArgs sa;
+  __shared__ int soff[kMaxSharedOffsets];
+  const int* off = stage_offsets(g, soff);
+  int cur = -1;  // instance whose arguments sa holds (uniform over the block)
   for (int vb = blockIdx.x; vb < g.total; vb += gridDim.x) {
-    const int k = find_instance(g, vb);
-    stage_args(&sa, &va[g.inst[k] * nstages + stage]);
-    __syncthreads();
-    vol_body<D, N, R, TT>(sa, vb - g.off[k], smem_raw);
-    __syncthreads();  // shared memory is reused by the next virtual block
+    const int k = find_instance(off, g.n, vb);
+    if (k != cur) {
+      stage_args(&sa, &va[g.inst[k] * nstages + stage]);
+      __syncthreads();
+      cur = k;
+    }
+    vol_body<D, N, R, TT>(sa, vb - off[k], smem_raw);
+    __syncthreads();  // shared memory (and sa) are reused by the next virtual block
   }
 }
 
@@ -68,24 +109,31 @@ __global__ void __launch_bounds__(256)
 batch_flux_kernel(const FluxArgs* fa, int nstages, int stage, BatchGroupArgs g) {
   constexpr int NF = IPow<N, D - 1>::value;
   __shared__ __align__(16) FluxArgs sa;
+  __shared__ int soff[kMaxSharedOffsets];
+  const int* off = stage_offsets(g, soff);
+  int cur = -1;  // instance whose arguments sa holds (uniform over the block)
   for (int vb = blockIdx.x; vb < g.total; vb += gridDim.x) {
-    const int k = find_instance(g, vb);
-    stage_args(&sa, &fa[g.inst[k] * nstages + stage]);
-    __syncthreads();
+    const int k = find_instance(off, g.n, vb);
+    if (k != cur) {
+      __syncthreads();  // every thread is done with the previous instance's arguments
+      stage_args(&sa, &fa[g.inst[k] * nstages + stage]);
+      __syncthreads();
+      cur = k;
+    }
     const int bpd = ((int)sa.m.ne * NF + 255) / 256;
-    const int local = vb - g.off[k];
+    const int local = vb - off[k];
     const int d = local / bpd;
     flux_body<D, N, R>(sa, local - d * bpd, d);
-    __syncthreads();
   }
 }
 
 // Launchers over (dim, N, TT) for one arithmetic (2D and 3D, TT in {64, 128, 256}).
 template <typename R>
 struct BatchDispatch {
+  // occ != nullptr: no launch; *occ = resident blocks per SM of the kernel
   template <int D, int N, int TT>
   static cudaError_t vol_t(const VolArgs* va, int ns, int st, const BatchGroupArgs& g, int grid,
-                           cudaStream_t s) {
+                           cudaStream_t s, int* occ) {
     using T = Tile<D, N, TT>;
     const size_t smem = sizeof(R) * T::EPB * D * T::NV * T::ND;
     if (smem > 48 * 1024) {
@@ -93,67 +141,71 @@ struct BatchDispatch {
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
     }
+    if (occ)
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, batch_vol_kernel<D, N, R, TT>,
+                                                           T::THREADS, smem);
     batch_vol_kernel<D, N, R, TT><<<grid, T::THREADS, smem, s>>>(va, ns, st, g);
     return cudaGetLastError();
   }
   template <int D, int N>
   static cudaError_t flux_t(const FluxArgs* fa, int ns, int st, const BatchGroupArgs& g, int grid,
-                            cudaStream_t s) {
+                            cudaStream_t s, int* occ) {
+    if (occ) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, batch_flux_kernel<D, N, R>, 256, 0);
     batch_flux_kernel<D, N, R><<<grid, 256, 0, s>>>(fa, ns, st, g);
     return cudaGetLastError();
   }
   template <int D, int N>
   static cudaError_t vol_tt(int tt, const VolArgs* va, int ns, int st, const BatchGroupArgs& g,
-                            int grid, cudaStream_t s) {
+                            int grid, cudaStream_t s, int* occ) {
     switch (tt) {
-      case 64: return vol_t<D, N, 64>(va, ns, st, g, grid, s);
-      case 128: return vol_t<D, N, 128>(va, ns, st, g, grid, s);
-      case 256: return vol_t<D, N, 256>(va, ns, st, g, grid, s);
+      case 64: return vol_t<D, N, 64>(va, ns, st, g, grid, s, occ);
+      case 128: return vol_t<D, N, 128>(va, ns, st, g, grid, s, occ);
+      case 256: return vol_t<D, N, 256>(va, ns, st, g, grid, s, occ);
     }
     return cudaErrorInvalidValue;
   }
   static cudaError_t vol(int dim, int N, int tt, const VolArgs* va, int ns, int st,
-                         const BatchGroupArgs& g, int grid, cudaStream_t s) {
+                         const BatchGroupArgs& g, int grid, cudaStream_t s, int* occ) {
     if (dim == 2) {
       switch (N) {
-        case 2: return vol_tt<2, 2>(tt, va, ns, st, g, grid, s);
-        case 3: return vol_tt<2, 3>(tt, va, ns, st, g, grid, s);
-        case 4: return vol_tt<2, 4>(tt, va, ns, st, g, grid, s);
-        case 5: return vol_tt<2, 5>(tt, va, ns, st, g, grid, s);
-        case 6: return vol_tt<2, 6>(tt, va, ns, st, g, grid, s);
-        case 7: return vol_tt<2, 7>(tt, va, ns, st, g, grid, s);
-        case 8: return vol_tt<2, 8>(tt, va, ns, st, g, grid, s);
+        case 2: return vol_tt<2, 2>(tt, va, ns, st, g, grid, s, occ);
+        case 3: return vol_tt<2, 3>(tt, va, ns, st, g, grid, s, occ);
+        case 4: return vol_tt<2, 4>(tt, va, ns, st, g, grid, s, occ);
+        case 5: return vol_tt<2, 5>(tt, va, ns, st, g, grid, s, occ);
+        case 6: return vol_tt<2, 6>(tt, va, ns, st, g, grid, s, occ);
+        case 7: return vol_tt<2, 7>(tt, va, ns, st, g, grid, s, occ);
+        case 8: return vol_tt<2, 8>(tt, va, ns, st, g, grid, s, occ);
       }
     } else if (dim == 3) {
       switch (N) {
-        case 2: return vol_tt<3, 2>(tt, va, ns, st, g, grid, s);
-        case 3: return vol_tt<3, 3>(tt, va, ns, st, g, grid, s);
-        case 4: return vol_tt<3, 4>(tt, va, ns, st, g, grid, s);
-        case 5: return vol_tt<3, 5>(tt, va, ns, st, g, grid, s);
-        case 6: return vol_tt<3, 6>(tt, va, ns, st, g, grid, s);
+        case 2: return vol_tt<3, 2>(tt, va, ns, st, g, grid, s, occ);
+        case 3: return vol_tt<3, 3>(tt, va, ns, st, g, grid, s, occ);
+        case 4: return vol_tt<3, 4>(tt, va, ns, st, g, grid, s, occ);
+        case 5: return vol_tt<3, 5>(tt, va, ns, st, g, grid, s, occ);
+        case 6: return vol_tt<3, 6>(tt, va, ns, st, g, grid, s, occ);
       }
     }
     return cudaErrorInvalidValue;
   }
   static cudaError_t flux(int dim, int N, const FluxArgs* fa, int ns, int st,
-                          const BatchGroupArgs& g, int grid, cudaStream_t s) {
+                          const BatchGroupArgs& g, int grid, cudaStream_t s, int* occ) {
     if (dim == 2) {
       switch (N) {
-        case 2: return flux_t<2, 2>(fa, ns, st, g, grid, s);
-        case 3: return flux_t<2, 3>(fa, ns, st, g, grid, s);
-        case 4: return flux_t<2, 4>(fa, ns, st, g, grid, s);
-        case 5: return flux_t<2, 5>(fa, ns, st, g, grid, s);
-        case 6: return flux_t<2, 6>(fa, ns, st, g, grid, s);
-        case 7: return flux_t<2, 7>(fa, ns, st, g, grid, s);
-        case 8: return flux_t<2, 8>(fa, ns, st, g, grid, s);
+        case 2: return flux_t<2, 2>(fa, ns, st, g, grid, s, occ);
+        case 3: return flux_t<2, 3>(fa, ns, st, g, grid, s, occ);
+        case 4: return flux_t<2, 4>(fa, ns, st, g, grid, s, occ);
+        case 5: return flux_t<2, 5>(fa, ns, st, g, grid, s, occ);
+        case 6: return flux_t<2, 6>(fa, ns, st, g, grid, s, occ);
+        case 7: return flux_t<2, 7>(fa, ns, st, g, grid, s, occ);
+        case 8: return flux_t<2, 8>(fa, ns, st, g, grid, s, occ);
       }
     } else if (dim == 3) {
       switch (N) {
-        case 2: return flux_t<3, 2>(fa, ns, st, g, grid, s);
-        case 3: return flux_t<3, 3>(fa, ns, st, g, grid, s);
-        case 4: return flux_t<3, 4>(fa, ns, st, g, grid, s);
-        case 5: return flux_t<3, 5>(fa, ns, st, g, grid, s);
-        case 6: return flux_t<3, 6>(fa, ns, st, g, grid, s);
+        case 2: return flux_t<3, 2>(fa, ns, st, g, grid, s, occ);
+        case 3: return flux_t<3, 3>(fa, ns, st, g, grid, s, occ);
+        case 4: return flux_t<3, 4>(fa, ns, st, g, grid, s, occ);
+        case 5: return flux_t<3, 5>(fa, ns, st, g, grid, s, occ);
+        case 6: return flux_t<3, 6>(fa, ns, st, g, grid, s, occ);
       }
     }
     return cudaErrorInvalidValue;

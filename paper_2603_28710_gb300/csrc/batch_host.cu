@@ -17,12 +17,12 @@
 #include "solver_internal.h"
 
 namespace adg {
-cudaError_t batch_vol_fp64(int, int, int, const VolArgs*, int, int, const BatchGroupArgs&, int, cudaStream_t);
-cudaError_t batch_vol_fp32(int, int, int, const VolArgs*, int, int, const BatchGroupArgs&, int, cudaStream_t);
-cudaError_t batch_vol_df64(int, int, int, const VolArgs*, int, int, const BatchGroupArgs&, int, cudaStream_t);
-cudaError_t batch_flux_fp64(int, int, const FluxArgs*, int, int, const BatchGroupArgs&, int, cudaStream_t);
-cudaError_t batch_flux_fp32(int, int, const FluxArgs*, int, int, const BatchGroupArgs&, int, cudaStream_t);
-cudaError_t batch_flux_df64(int, int, const FluxArgs*, int, int, const BatchGroupArgs&, int, cudaStream_t);
+cudaError_t batch_vol_fp64(int, int, int, const VolArgs*, int, int, const BatchGroupArgs&, int, cudaStream_t, int*);
+cudaError_t batch_vol_fp32(int, int, int, const VolArgs*, int, int, const BatchGroupArgs&, int, cudaStream_t, int*);
+cudaError_t batch_vol_df64(int, int, int, const VolArgs*, int, int, const BatchGroupArgs&, int, cudaStream_t, int*);
+cudaError_t batch_flux_fp64(int, int, const FluxArgs*, int, int, const BatchGroupArgs&, int, cudaStream_t, int*);
+cudaError_t batch_flux_fp32(int, int, const FluxArgs*, int, int, const BatchGroupArgs&, int, cudaStream_t, int*);
+cudaError_t batch_flux_df64(int, int, const FluxArgs*, int, int, const BatchGroupArgs&, int, cudaStream_t, int*);
 void noalloc_set_error(const char* msg);
 
 namespace {
@@ -60,22 +60,23 @@ __global__ void batch_schedule_kernel(BatchSched* sc, FluxArgs* fa, int nstages,
   sc[i] = s;
 }
 
+// occ != nullptr: no launch, *occ = resident blocks per SM of the kernel
 cudaError_t vol_launch(int prec, int dim, int N, int tt, const VolArgs* va, int ns, int st,
-                       const BatchGroupArgs& g, int grid, cudaStream_t s) {
+                       const BatchGroupArgs& g, int grid, cudaStream_t s, int* occ = nullptr) {
   switch (prec) {
-    case 0: return batch_vol_fp64(dim, N, tt, va, ns, st, g, grid, s);
-    case 1: return batch_vol_fp32(dim, N, tt, va, ns, st, g, grid, s);
-    case 2: return batch_vol_df64(dim, N, tt, va, ns, st, g, grid, s);
+    case 0: return batch_vol_fp64(dim, N, tt, va, ns, st, g, grid, s, occ);
+    case 1: return batch_vol_fp32(dim, N, tt, va, ns, st, g, grid, s, occ);
+    case 2: return batch_vol_df64(dim, N, tt, va, ns, st, g, grid, s, occ);
   }
   return cudaErrorInvalidValue;
 }
 
 cudaError_t flux_launch(int prec, int dim, int N, const FluxArgs* fa, int ns, int st,
-                        const BatchGroupArgs& g, int grid, cudaStream_t s) {
+                        const BatchGroupArgs& g, int grid, cudaStream_t s, int* occ = nullptr) {
   switch (prec) {
-    case 0: return batch_flux_fp64(dim, N, fa, ns, st, g, grid, s);
-    case 1: return batch_flux_fp32(dim, N, fa, ns, st, g, grid, s);
-    case 2: return batch_flux_df64(dim, N, fa, ns, st, g, grid, s);
+    case 0: return batch_flux_fp64(dim, N, fa, ns, st, g, grid, s, occ);
+    case 1: return batch_flux_fp32(dim, N, fa, ns, st, g, grid, s, occ);
+    case 2: return batch_flux_df64(dim, N, fa, ns, st, g, grid, s, occ);
   }
   return cudaErrorInvalidValue;
 }
@@ -105,12 +106,16 @@ struct adg_batch {
   std::vector<int64_t> inst_steps;  // steps taken since each instance's state was set
   struct Group {
     int N = 0, tt = 128;
-    std::vector<int> inst;
+    std::vector<int> inst;   // all instances of the degree (face-flux launch)
+    std::vector<int> vinst;  // instances in the persistent volume launch
+    std::vector<int> solo;   // instances with a volume launch of their own
     int* inst_dev = nullptr;
+    int* vinst_dev = nullptr;
     int* voff_dev = nullptr;
     int* foff_dev = nullptr;
     int vtotal = 0, ftotal = 0;
     int vgrid = 0, fgrid = 0;
+    int vpersist = 1, fpersist = 1;  // one resident wave looping over tiles, or a block per tile
   };
   std::vector<Group> groups;
   cudaGraphExec_t exec = nullptr;
@@ -146,6 +151,7 @@ void free_batch(adg_batch* b) {
   drop_graph(b);
   for (auto& g : b->groups) {
     if (g.inst_dev) cudaFree(g.inst_dev);
+    if (g.vinst_dev) cudaFree(g.vinst_dev);
     if (g.voff_dev) cudaFree(g.voff_dev);
     if (g.foff_dev) cudaFree(g.foff_dev);
   }
@@ -155,7 +161,9 @@ void free_batch(adg_batch* b) {
   for (adg_solver* s : b->inst) adg_destroy(s);
 }
 
-// persistent grid: enough blocks to fill every SM a few times, never more than needed
+// persistent grid: one wave of resident blocks (per_sm from the occupancy calculator), never
+// more blocks than virtual blocks; a second partial wave would run a share of the work at
+// low occupancy after the first wave ends
 int persistent_grid(int total, int per_sm) {
   int dev = 0, sms = 152;
   if (cudaGetDevice(&dev) == cudaSuccess)
@@ -163,22 +171,42 @@ int persistent_grid(int total, int per_sm) {
   return std::max(1, std::min(total, sms * per_sm));
 }
 
-// virtual-block offsets of a group for the chosen tile
+// An instance whose volume tiles fill the GPU this many times over gets a volume launch of
+// its own (arguments in the kernel's parameter bank) instead of a share of the persistent
+// launch: a persistent block reads its instance's arguments from shared memory, which costs
+// registers and hence occupancy, while small instances gain more from sharing one launch.
+constexpr int kSoloWaves = 4;
+
+// Split of a group into batched and solo volume work, and virtual-block offsets, for the
+// chosen tile and launch shapes.
 adg_status layout_group(adg_batch* b, adg_batch::Group& g) {
   const int nd = ipow(g.N, b->dim), nf = nd / g.N;
   const int epb = std::max(1, g.tt / nd);
-  std::vector<int> voff(g.inst.size() + 1), foff(g.inst.size() + 1);
-  voff[0] = foff[0] = 0;
-  for (size_t k = 0; k < g.inst.size(); ++k) {
-    const int64_t ne = b->inst[g.inst[k]]->ne;
-    voff[k + 1] = voff[k] + (int)((ne + epb - 1) / epb);
-    foff[k + 1] = foff[k] + b->dim * (int)((ne * nf + 255) / 256);
+  int vocc = 0, focc = 0, dev = 0, sms = 152;
+  BCUDA(b, vol_launch(b->prec, b->dim, g.N, g.tt, nullptr, 0, 0, BatchGroupArgs{}, 0, 0, &vocc));
+  BCUDA(b, flux_launch(b->prec, b->dim, g.N, nullptr, 0, 0, BatchGroupArgs{}, 0, 0, &focc));
+  if (cudaGetDevice(&dev) == cudaSuccess)
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t wave = (int64_t)sms * std::max(1, vocc);
+  g.vinst.clear();
+  g.solo.clear();
+  for (int i : g.inst) {
+    const int64_t tiles = (b->inst[i]->ne + epb - 1) / epb;
+    (tiles >= kSoloWaves * wave ? g.solo : g.vinst).push_back(i);
   }
+  std::vector<int> voff(g.vinst.size() + 1), foff(g.inst.size() + 1);
+  voff[0] = foff[0] = 0;
+  for (size_t k = 0; k < g.vinst.size(); ++k)
+    voff[k + 1] = voff[k] + (int)((b->inst[g.vinst[k]]->ne + epb - 1) / epb);
+  for (size_t k = 0; k < g.inst.size(); ++k)
+    foff[k + 1] = foff[k] + b->dim * (int)((b->inst[g.inst[k]]->ne * nf + 255) / 256);
   g.vtotal = voff.back();
   g.ftotal = foff.back();
-  const int threads = epb * nd;
-  g.vgrid = persistent_grid(g.vtotal, std::max(1, 2048 / threads));
-  g.fgrid = persistent_grid(g.ftotal, 8);
+  g.vgrid = g.vpersist ? persistent_grid(g.vtotal, std::max(1, vocc)) : g.vtotal;
+  g.fgrid = g.fpersist ? persistent_grid(g.ftotal, std::max(1, focc)) : g.ftotal;
+  if (!g.vinst.empty())
+    BCUDA(b, cudaMemcpy(g.vinst_dev, g.vinst.data(), g.vinst.size() * sizeof(int),
+                        cudaMemcpyHostToDevice));
   BCUDA(b, cudaMemcpy(g.voff_dev, voff.data(), voff.size() * sizeof(int), cudaMemcpyHostToDevice));
   BCUDA(b, cudaMemcpy(g.foff_dev, foff.data(), foff.size() * sizeof(int), cudaMemcpyHostToDevice));
   return ADG_OK;
@@ -186,11 +214,21 @@ adg_status layout_group(adg_batch* b, adg_batch::Group& g) {
 
 BatchGroupArgs group_args(const adg_batch::Group& g, bool vol) {
   BatchGroupArgs a;
-  a.inst = g.inst_dev;
+  a.inst = vol ? g.vinst_dev : g.inst_dev;
   a.off = vol ? g.voff_dev : g.foff_dev;
-  a.n = (int)g.inst.size();
+  a.n = (int)(vol ? g.vinst.size() : g.inst.size());
   a.total = vol ? g.vtotal : g.ftotal;
   return a;
+}
+
+// volume work of a group at stage m: the persistent launch and the solo launches
+adg_status vol_group(adg_batch* b, adg_batch::Group& g, int m, cudaStream_t s) {
+  if (!g.vinst.empty())
+    BCUDA(b, vol_launch(b->prec, b->dim, g.N, g.tt, b->va_dev, b->stages, m, group_args(g, true),
+                        g.vgrid, s));
+  for (int i : g.solo)
+    BCUDA(b, launch_vol(b->prec, b->dim, g.N, b->va_host[i * b->stages + m], s));
+  return ADG_OK;
 }
 
 // enqueue one full step: schedule kernel, then flux and volume launches of every group
@@ -201,9 +239,10 @@ adg_status enqueue_step(adg_batch* b, cudaStream_t s) {
     for (auto& g : b->groups)
       BCUDA(b, flux_launch(b->prec, b->dim, g.N, b->fa_dev, b->stages, m, group_args(g, false),
                            g.fgrid, s));
-    for (auto& g : b->groups)
-      BCUDA(b, vol_launch(b->prec, b->dim, g.N, g.tt, b->va_dev, b->stages, m,
-                          group_args(g, true), g.vgrid, s));
+    for (auto& g : b->groups) {
+      adg_status st = vol_group(b, g, m, s);
+      if (st != ADG_OK) return st;
+    }
   }
   return ADG_OK;
 }
@@ -257,6 +296,7 @@ adg_status refresh_instance(adg_batch* b, int i) {
   BCUDA(b, cudaMemcpyAsync(b->sc_dev + i, &b->sc_host[i], sizeof(BatchSched),
                            cudaMemcpyHostToDevice, b->stream));
   BCUDA(b, cudaStreamSynchronize(b->stream));
+  drop_graph(b);  // solo volume launches hold the instance's arguments by value
   b->has_state[i] = 1;
   b->inst_steps[i] = 0;
   return ADG_OK;
@@ -317,6 +357,7 @@ adg_status adg_batch_create(int n, const adg_mesh* meshes, const int* degrees, c
     g.inst = kv.second;
     const size_t k = g.inst.size();
     if (ce == cudaSuccess) ce = cudaMalloc((void**)&g.inst_dev, k * sizeof(int));
+    if (ce == cudaSuccess) ce = cudaMalloc((void**)&g.vinst_dev, k * sizeof(int));
     if (ce == cudaSuccess) ce = cudaMalloc((void**)&g.voff_dev, (k + 1) * sizeof(int));
     if (ce == cudaSuccess) ce = cudaMalloc((void**)&g.foff_dev, (k + 1) * sizeof(int));
     if (ce == cudaSuccess) ce = cudaMemcpy(g.inst_dev, g.inst.data(), k * sizeof(int), cudaMemcpyHostToDevice);
@@ -392,33 +433,58 @@ adg_status adg_batch_autotune(adg_batch* b, int trials, int* tile_threads) {
   cudaEvent_t e0, e1;
   BCUDA(b, cudaEventCreate(&e0));
   BCUDA(b, cudaEventCreate(&e1));
+  // time `trials` launches (after one warm-up) of the group's volume work at stage 0 (it
+  // reads only the solution, never the RK register: the persistent launch and the solo
+  // launches of its split for the tile) or of its face-flux kernel
+  auto time_group = [&](adg_batch::Group& g, bool vol, float* ms) -> adg_status {
+    for (int t = 0; t <= trials; ++t) {
+      if (t == 1) BCUDA(b, cudaEventRecord(e0, b->stream));
+      if (vol) {
+        adg_status st = vol_group(b, g, 0, b->stream);
+        if (st != ADG_OK) return st;
+      } else
+        BCUDA(b, flux_launch(b->prec, b->dim, g.N, b->fa_dev, b->stages, 0,
+                             group_args(g, false), g.fgrid, b->stream));
+    }
+    BCUDA(b, cudaEventRecord(e1, b->stream));
+    BCUDA(b, cudaEventSynchronize(e1));
+    BCUDA(b, cudaEventElapsedTime(ms, e0, e1));
+    return ADG_OK;
+  };
   const int cand[3] = {64, 128, 256};
   for (size_t gi = 0; gi < b->groups.size(); ++gi) {
     auto& g = b->groups[gi];
-    float best = 1e30f;
-    int best_tt = 128;
-    for (int tt : cand) {
-      g.tt = tt;
+    float best = 1e30f, ms = 0.f;
+    int best_tt = 128, best_vp = 1, best_fp = 1;
+    // volume kernel: tile size x launch shape
+    for (int tt : cand)
+      for (int vp = 1; vp >= 0; --vp) {
+        g.tt = tt;
+        g.vpersist = vp;
+        adg_status st = layout_group(b, g);
+        if (st == ADG_OK) st = time_group(g, true, &ms);
+        if (st != ADG_OK) return st;
+        if (ms < best) {
+          best = ms;
+          best_tt = tt;
+          best_vp = vp;
+        }
+      }
+    g.tt = best_tt;
+    g.vpersist = best_vp;
+    // face-flux kernel: launch shape
+    best = 1e30f;
+    for (int fp = 1; fp >= 0; --fp) {
+      g.fpersist = fp;
       adg_status st = layout_group(b, g);
+      if (st == ADG_OK) st = time_group(g, false, &ms);
       if (st != ADG_OK) return st;
-      // warm-up, then time `trials` launches of the group's volume kernel (stage 0: it
-      // reads only the solution, never the RK register)
-      BCUDA(b, vol_launch(b->prec, b->dim, g.N, g.tt, b->va_dev, b->stages, 0,
-                          group_args(g, true), g.vgrid, b->stream));
-      BCUDA(b, cudaEventRecord(e0, b->stream));
-      for (int t = 0; t < trials; ++t)
-        BCUDA(b, vol_launch(b->prec, b->dim, g.N, g.tt, b->va_dev, b->stages, 0,
-                            group_args(g, true), g.vgrid, b->stream));
-      BCUDA(b, cudaEventRecord(e1, b->stream));
-      BCUDA(b, cudaEventSynchronize(e1));
-      float ms = 0.f;
-      BCUDA(b, cudaEventElapsedTime(&ms, e0, e1));
       if (ms < best) {
         best = ms;
-        best_tt = tt;
+        best_fp = fp;
       }
     }
-    g.tt = best_tt;
+    g.fpersist = best_fp;
     adg_status st = layout_group(b, g);
     if (st != ADG_OK) return st;
     if (tile_threads) tile_threads[gi] = best_tt;

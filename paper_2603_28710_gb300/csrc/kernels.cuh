@@ -45,11 +45,13 @@ __device__ __forceinline__ void elem_coords(const MeshArgs& m, int e, int* c) {
 }
 
 // index of the neighbour of element e (coordinates c) one step s (+1/-1) along d, periodic
+// (selects instead of indexing c by a runtime d keep c in registers)
 __device__ __forceinline__ int elem_shift(const MeshArgs& m, int e, const int* c, int d, int s) {
-  int k = c[d] + s;
+  const int cd = d == 0 ? c[0] : (d == 1 ? c[1] : c[2]);
+  int k = cd + s;
   if (k < 0) k += m.n[d];
   if (k >= m.n[d]) k -= m.n[d];
-  return e + (k - c[d]) * (int)m.es[d];
+  return e + (k - cd) * (int)m.es[d];
 }
 
 // Pointwise Euler flux columns F_d(w), d < D (Eq. 2-3, no source).
