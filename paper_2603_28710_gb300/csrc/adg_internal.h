@@ -42,7 +42,20 @@ struct MeshArgs {
   int n[3];
   int64_t ne;
   int64_t es[3];  // element index stride per direction
+  // Division by n[0] and n[1] as a multiply-high (division by invariant integers, Granlund
+  // & Montgomery, PLDI 1994): q = floor(e / n) = umulhi64(e, M) with M = ceil(2^64 / n),
+  // exact for e < 2^64 / n, hence for every 32-bit e when n < 2^31; n = 1 is special-cased.
+  uint64_t divm[2];
 };
+
+// Fills es[] and divm[] from n[] (host side).
+inline void mesh_finish(MeshArgs& m) {
+  m.es[0] = 1;
+  m.es[1] = m.n[0];
+  m.es[2] = (int64_t)m.n[0] * m.n[1];
+  for (int i = 0; i < 2; ++i)
+    m.divm[i] = m.n[i] > 1 ? ~0ull / (uint64_t)m.n[i] + 1ull : 0ull;
+}
 
 enum UpdateMode { kModeRHS = 0, kMode2R = 1, kMode2N = 2 };
 

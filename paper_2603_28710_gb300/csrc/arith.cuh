@@ -91,9 +91,19 @@ __device__ __forceinline__ double r_rcp(double x) {
   e = fma(-x, r, 1.0);
   return fma(r, e, r);
 }
-__device__ __forceinline__ float r_rcp(float x) { return 1.0f / x; }
+// FP32 operator: the hardware approximations (PTX rcp.approx / sqrt.approx, at most one
+// ulp and 2^-23 relative error), one instruction each instead of the IEEE sequences.
+__device__ __forceinline__ float r_rcp(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 __device__ __forceinline__ double r_sqrt(double x) { return sqrt(x); }
-__device__ __forceinline__ float r_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ float r_sqrt(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 __device__ __forceinline__ double r_max(double a, double b) { return fmax(a, b); }
 __device__ __forceinline__ float r_max(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ double r_fma(double a, double b, double c) { return fma(a, b, c); }

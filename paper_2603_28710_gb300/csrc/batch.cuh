@@ -63,24 +63,16 @@ __device__ __forceinline__ void stage_args(T* dst, const T* src) {
 
 // Register budget of the batched volume kernels.  The persistent loop and the arguments
 // read from shared memory raise their register use over the single-instance kernels (FP32:
-// 48 against 32 at 128 threads, over 90 for tiles of 64 threads), which cuts the occupancy
-// the latency-bound FP32 form needs.  Caps without spills (ptxas, sm_103a): 40 registers
-// in 2D, 48 at N = 4 and 8 and for tiles of at most 64 threads; 3D stays uncapped (40
-// spills at N = 6).
-template <int D, int N, typename R> struct VolRegs { static constexpr int value = 0; };
-template <int D, int N> struct VolRegs<D, N, float> {
-  static constexpr int value = D != 2 ? 0 : ((N == 4 || N == 8) ? 48 : 40);
+// 48 against 32 at 128 threads, over 90 for tiles of 64 threads when left to the
+// compiler), which cuts the occupancy the latency-bound FP32 form needs.  Budgets without
+// spills (ptxas, sm_103a): FP32 40 registers in 2D (48 at N = 4 and 8 and for tiles of at
+// most 64 threads), 56 in 3D; FP64 and FP32 pairs 16 above the single-instance budget.
+template <int D, int N, typename R> struct VolRegs {
+  static constexpr int value = VolKernelRegs<D, N, R>::value + 16;
 };
-
-// blocks per SM that leave `regs` registers per thread: each of the 4 SM sub-partitions
-// holds 16384 registers and a whole number of warps
-constexpr int min_blocks_for(int regs, int threads) {
-  if (regs == 0) return 1;
-  if (threads <= 64 && regs < 48) regs = 48;
-  const int warps = (threads + 31) / 32;
-  const int b = (16384 / (regs * 32)) * 4 / warps;
-  return b < 1 ? 1 : (b > 32 ? 32 : b);
-}
+template <int D, int N> struct VolRegs<D, N, float> {
+  static constexpr int value = D != 2 ? 56 : ((N == 4 || N == 8) ? 48 : 40);
+};
 
 template <int D, int N, typename R, int TT>
 __global__ void __launch_bounds__(Tile<D, N, TT>::THREADS,

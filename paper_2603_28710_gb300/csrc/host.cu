@@ -576,9 +576,7 @@ adg_status adg_create(const adg_mesh* mesh, int degree, const int P[3], int max_
   s->margs.n[1] = mesh->n_elem[1];
   s->margs.n[2] = s->dim == 3 ? mesh->n_elem[2] : 1;
   s->margs.ne = ne;
-  s->margs.es[0] = 1;
-  s->margs.es[1] = s->margs.n[0];
-  s->margs.es[2] = (int64_t)s->margs.n[0] * s->margs.n[1];
+  mesh_finish(s->margs);
   build_tables(s);
 
   // subdomain faces: face (d, e) joins e and its +d neighbour; it lies between two

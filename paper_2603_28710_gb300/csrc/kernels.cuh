@@ -14,6 +14,7 @@
 //                 face traces of the next stage input.
 // Index arithmetic is 32-bit: the host rejects meshes with 2^31 or more degrees of freedom.
 #pragma once
+#include <type_traits>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -37,10 +38,25 @@ struct Tile {
   static constexpr int THREADS = EPB * ND;
 };
 
+// floor(e / m.n[i]) for 0 <= e < 2^31 (multiply-high by the precomputed inverse)
+__device__ __forceinline__ int mesh_div(const MeshArgs& m, int i, int e) {
+  return m.n[i] == 1 ? e : (int)__umul64hi((unsigned long long)(unsigned)e, m.divm[i]);
+}
+
+// Blocks per SM that leave `regs` registers per thread (0: no budget): each of the 4 SM
+// sub-partitions holds 16384 registers and a whole number of warps.
+constexpr int min_blocks_for(int regs, int threads) {
+  if (regs == 0) return 1;
+  if (threads <= 64 && regs < 48) regs = 48;
+  const int warps = (threads + 31) / 32;
+  const int b = (16384 / (regs * 32)) * 4 / warps;
+  return b < 1 ? 1 : (b > 32 ? 32 : b);
+}
+
 __device__ __forceinline__ void elem_coords(const MeshArgs& m, int e, int* c) {
-  const int q = e / m.n[0];
+  const int q = mesh_div(m, 0, e);
   c[0] = e - q * m.n[0];
-  c[2] = q / m.n[1];
+  c[2] = mesh_div(m, 1, q);
   c[1] = q - c[2] * m.n[1];
 }
 
@@ -166,30 +182,63 @@ __device__ __forceinline__ void store_trace(float2* p, double v) {
 __device__ __forceinline__ void store_trace(float2* p, df64 v) { *p = make_float2(v.hi, v.lo); }
 
 // Traces of a tile of elements held in shared memory sX[el][v][node] (compute type C) -> tr.
+// FP32 and FP32-pair operators: a thread owns one (direction, side, variable, face node)
+// combination, so its line of nodes, stride and interpolation weights are set up once, and
+// interpolates it for a run of the tile's elements (the runs split the elements when the
+// block has threads to spare); this halves their instruction count in this phase.  The
+// FP64 operator is bound by its FP64 pipe, not by issue, and keeps one flat loop over all
+// (element, face node) items, which spreads the FP64 work over every thread.
 template <int D, int N, typename R, int TT = 128, typename C = R>
 __device__ __forceinline__ void write_traces(const MeshArgs& m, const OpTables* tab, const C* sX,
                                              int e0, typename Arith<R>::S* tr) {
   using T = Tile<D, N, TT>;
   constexpr int ND = T::ND, NF = T::NF, NV = T::NV, EPB = T::EPB;
-  constexpr int TOTAL = EPB * 2 * D * NV * NF;
   const int ne = (int)m.ne;
-  for (int g = threadIdx.x; g < TOTAL; g += blockDim.x) {
-    const int jj = g % (EPB * NF);
-    const int rest = g / (EPB * NF);  // (d*2 + side)*NV + v
-    const int el = jj / NF, j = jj - el * NF;
-    const int e = e0 + el;
-    if (e >= ne) continue;
-    const int v = rest % NV, ds = rest / NV;
-    const int d = ds >> 1, side = ds & 1;
-    const int base = line_base<D, N>(d, j);
-    const int stride = d == 0 ? 1 : (d == 1 ? N : N * N);
-    const double* tw = side ? tab->Tp : tab->Tm;
-    const float2* twf = side ? tab->Tpf : tab->Tmf;
-    typename Arith<C>::Acc acc = acc_zero(typename Arith<C>::Acc());
+  if constexpr (std::is_same<R, double>::value) {
+    constexpr int TOTAL = EPB * 2 * D * NV * NF;
+    for (int g = threadIdx.x; g < TOTAL; g += blockDim.x) {
+      const int jj = g % (EPB * NF);
+      const int rest = g / (EPB * NF);  // (d*2 + side)*NV + v
+      const int el = jj / NF, j = jj - el * NF;
+      const int e = e0 + el;
+      if (e >= ne) continue;
+      const int v = rest % NV, ds = rest / NV;
+      const int d = ds >> 1, side = ds & 1;
+      const int base = line_base<D, N>(d, j);
+      const int stride = d == 0 ? 1 : (d == 1 ? N : N * N);
+      const double* tw = side ? tab->Tp : tab->Tm;
+      double acc = 0.0;
 #pragma unroll
-    for (int a = 0; a < N; ++a)
-      acc = acc_fma(Arith<C>::tab(tw, twf, a), sX[(el * NV + v) * ND + base + a * stride], acc);
-    store_trace(tr + ((ds * NV + v) * ne + e) * NF + j, acc_result(acc));
+      for (int a = 0; a < N; ++a) acc = fma(tw[a], sX[(el * NV + v) * ND + base + a * stride], acc);
+      store_trace(tr + ((ds * NV + v) * ne + e) * NF + j, acc);
+    }
+  } else {
+    constexpr int CT = 2 * D * NV * NF;                            // combinations
+    constexpr int CH = T::THREADS / CT > 0 ? T::THREADS / CT : 1;  // element runs
+    constexpr int RUN = (EPB + CH - 1) / CH;                       // elements per run
+    for (int g = threadIdx.x; g < CT * CH; g += blockDim.x) {
+      const int c = g % CT, ch = g / CT;
+      const int j = c % NF, rest = c / NF;  // rest = (d*2 + side)*NV + v
+      const int v = rest % NV, ds = rest / NV;
+      const int d = ds >> 1, side = ds & 1;
+      const int base = line_base<D, N>(d, j);
+      const int stride = d == 0 ? 1 : (d == 1 ? N : N * N);
+      const double* tw = side ? tab->Tp : tab->Tm;
+      const float2* twf = side ? tab->Tpf : tab->Tmf;
+      C t[N];
+#pragma unroll
+      for (int a = 0; a < N; ++a) t[a] = Arith<C>::tab(tw, twf, a);
+      const int el0 = ch * RUN;
+      const int el1 = el0 + RUN < EPB ? el0 + RUN : EPB;
+      typename Arith<R>::S* dst = tr + ((ds * NV + v) * ne + e0) * NF + j;
+      for (int el = el0; el < el1 && e0 + el < ne; ++el) {
+        const C* x = sX + (el * NV + v) * ND + base;
+        typename Arith<C>::Acc acc = acc_zero(typename Arith<C>::Acc());
+#pragma unroll
+        for (int a = 0; a < N; ++a) acc = acc_fma(t[a], x[a * stride], acc);
+        store_trace(dst + el * NF, acc_result(acc));
+      }
+    }
   }
 }
 
@@ -263,7 +312,13 @@ struct Update {
     A.w[idx] = w1;
     if (!A.last) Arith<R>::store(x + idx, q1);
     xd = w1;
-    return Arith<R>::from_double(w1);
+    if constexpr (std::is_same<R, float>::value) {
+      // FP32 operator: the next stage input (stage input u_in = w0 in FP32, plus the
+      // increment) within an FP32 ulp of float(w1), without a conversion
+      return r_fma(cB, q1, u_in);
+    } else {
+      return Arith<R>::from_double(w1);
+    }
   }
 };
 
@@ -343,10 +398,11 @@ __device__ __forceinline__ void vol_body(const VolArgs& A, int tile, unsigned ch
     for (int d = 0; d < D; ++d) {
       const int stride = d == 0 ? 1 : (d == 1 ? N : N * N);
       const int base = node - ix[d] * stride;
+      const double* Qd = (A.scaled ? A.tab->Qs[d] : A.tab->Q[d]) + ix[d] * N;
+      const float2* Qdf = (A.scaled ? A.tab->Qsf[d] : A.tab->Qf[d]) + ix[d] * N;
 #pragma unroll
       for (int a = 0; a < N; ++a) {
-        const R q = A.scaled ? Arith<R>::tab(A.tab->Qs[d], A.tab->Qsf[d], ix[d] * N + a)
-                             : Arith<R>::tab(A.tab->Q[d], A.tab->Qf[d], ix[d] * N + a);
+        const R q = Arith<R>::tab(Qd, Qdf, a);
 #pragma unroll
         for (int v = 0; v < NV; ++v)
           acc[v] = acc_fma(q, sF[((el * D + d) * NV + v) * ND + base + a * stride], acc[v]);
@@ -356,10 +412,10 @@ __device__ __forceinline__ void vol_body(const VolArgs& A, int tile, unsigned ch
     for (int d = 0; d < D; ++d) {
       const int j = face_index<D, N>(d, ix);
       const int elo = elem_shift(A.m, e, ec, d, -1);
-      const R lp = A.scaled ? Arith<R>::tab(A.tab->Lps[d], A.tab->Lpsf[d], ix[d])
-                            : Arith<R>::tab(A.tab->Lp[d], A.tab->Lpf[d], ix[d]);
-      const R lm = A.scaled ? Arith<R>::tab(A.tab->Lms[d], A.tab->Lmsf[d], ix[d])
-                            : Arith<R>::tab(A.tab->Lm[d], A.tab->Lmf[d], ix[d]);
+      const R lp = Arith<R>::tab(A.scaled ? A.tab->Lps[d] : A.tab->Lp[d],
+                                 A.scaled ? A.tab->Lpsf[d] : A.tab->Lpf[d], ix[d]);
+      const R lm = Arith<R>::tab(A.scaled ? A.tab->Lms[d] : A.tab->Lm[d],
+                                 A.scaled ? A.tab->Lmsf[d] : A.tab->Lmf[d], ix[d]);
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         const R fhi = Arith<R>::load(fl + ((d * NV + v) * ne + e) * NF + j);
@@ -392,8 +448,24 @@ __device__ __forceinline__ void vol_body(const VolArgs& A, int tile, unsigned ch
   }
 }
 
+// Register budget of the single-instance volume kernel (an explicit budget also keeps the
+// compiler from trading occupancy for registers).  The FP32 form is latency-bound and
+// wants every warp slot.
+template <int D, int N, typename R> struct VolKernelRegs {
+  static constexpr int value = D == 2 ? 48 : 56;
+};
+template <int D, int N> struct VolKernelRegs<D, N, double> {
+  static constexpr int value = D == 2 ? (N == 3 ? 48 : 40) : 56;  // no spills (ptxas, sm_103a)
+};
+template <int D, int N> struct VolKernelRegs<D, N, float> {
+  static constexpr int value = (D == 2 || N == 4) ? 32 : 40;  // no spills (ptxas, sm_103a)
+};
+
 template <int D, int N, typename R, int TT = 128>
-__global__ void __launch_bounds__(Tile<D, N, TT>::THREADS) vol_kernel(const VolArgs A) {
+__global__ void __launch_bounds__(Tile<D, N, TT>::THREADS,
+                                  min_blocks_for(VolKernelRegs<D, N, R>::value,
+                                                 Tile<D, N, TT>::THREADS))
+vol_kernel(const VolArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   vol_body<D, N, R, TT>(A, blockIdx.x, smem_raw);
 }
@@ -495,9 +567,15 @@ __device__ __forceinline__ void flux_body(const FluxArgs& A, int bx, int d) {
   for (int v = 0; v < NV; ++v) Arith<R>::store(fl + ((d * NV + v) * ne + e) * NF + j, f[v]);
 }
 
+// Register budget of the face-flux kernel (blocks of 256 threads; no spills, ptxas sm_103a).
+template <int D, typename R> struct FluxKernelRegs { static constexpr int value = 64; };
+template <int D> struct FluxKernelRegs<D, float> { static constexpr int value = 48; };
+template <int D> struct FluxKernelRegs<D, df64> { static constexpr int value = D == 2 ? 48 : 64; };
+
 // grid: x over (element, face node) of one direction, y = direction d
 template <int D, int N, typename R>
-__global__ void __launch_bounds__(256) flux_kernel(const FluxArgs A) {
+__global__ void __launch_bounds__(256, min_blocks_for(FluxKernelRegs<D, R>::value, 256))
+flux_kernel(const FluxArgs A) {
   flux_body<D, N, R>(A, blockIdx.x, blockIdx.y);
 }
 

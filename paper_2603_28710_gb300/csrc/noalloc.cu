@@ -103,9 +103,7 @@ extern "C" adg_status adg_rhs_noalloc(const adg_mesh* mesh, int degree, double g
   m.n[1] = mesh->n_elem[1];
   m.n[2] = dim == 3 ? mesh->n_elem[2] : 1;
   m.ne = ne;
-  m.es[0] = 1;
-  m.es[1] = m.n[0];
-  m.es[2] = (int64_t)m.n[0] * m.n[1];
+  mesh_finish(m);
 
   TraceArgs ta;
   std::memset(&ta, 0, sizeof(ta));
