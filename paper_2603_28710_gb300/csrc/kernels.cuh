@@ -167,6 +167,23 @@ __device__ __forceinline__ int face_index(int d, const int* ix) {
   return j;
 }
 
+// Asynchronous 4- and 8-byte copies global -> shared memory (cp.async; sm_80 and later).
+// The issuing thread waits for its own copies with cp_async_wait<n> (at most n of its
+// committed groups still pending); nothing spins.
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int n>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(n) : "memory");
+}
+
 // Arithmetic of the trace interpolation for an operator arithmetic R: the FP32-pair kernels
 // interpolate in native FP64 (their FP64 pipe is otherwise idle and the RK update hands
 // over the FP64 stage input), the others in R itself.
@@ -283,13 +300,16 @@ struct Update {
   using S = typename Arith<R>::S;
   // returns the next stage input at this node/variable; xd receives it in FP64 where the
   // update has it in FP64 (the FP32-pair traces use it)
-  __device__ static __forceinline__ R apply(const VolArgs& A, int idx, R k, R u_in, double& xd) {
+  // pre: the solution w0 and the 2N register q at this index were staged in advance (pw0,
+  // pq) by the volume kernel
+  __device__ static __forceinline__ R apply(const VolArgs& A, int idx, R k, R u_in, double& xd,
+                                            bool pre = false, double pw0 = 0.0, R pq = R(0.0f)) {
     if (A.mode == kModeRHS) {
       A.kout[idx] = Arith<R>::to_double(k);
       xd = Arith<R>::to_double(u_in);
       return u_in;
     }
-    const double w0 = A.w[idx];
+    const double w0 = pre ? pw0 : A.w[idx];
     S* x = reinterpret_cast<S*>(A.x);
     if (A.mode == kMode2R) {
       const R cb = Arith<R>::pair(A.cb, A.cbf), ca = Arith<R>::pair(A.ca, A.caf);
@@ -307,7 +327,7 @@ struct Update {
     }
     const R cA = Arith<R>::pair(A.ca, A.caf), cB = Arith<R>::pair(A.cb, A.cbf);
     const R dtk = A.scaled ? k : Arith<R>::pair(A.dt, A.dtf) * k;
-    const R q1 = (A.stage > 0) ? r_fma(cA, Arith<R>::load(x + idx), dtk) : dtk;
+    const R q1 = (A.stage > 0) ? r_fma(cA, pre ? pq : Arith<R>::load(x + idx), dtk) : dtk;
     const double w1 = add_increment(w0, cB * q1);
     A.w[idx] = w1;
     if (!A.last) Arith<R>::store(x + idx, q1);
@@ -325,7 +345,8 @@ struct Update {
 template <>
 struct Update<double> {
   __device__ static __forceinline__ double apply(const VolArgs& A, int idx, double k, double u_in,
-                                                 double& xd) {
+                                                 double& xd, bool = false, double = 0.0,
+                                                 double = 0.0) {
     xd = 0.0;
     if (A.mode == kModeRHS) {
       A.kout[idx] = k;
@@ -352,12 +373,32 @@ struct Update<double> {
 
 // One element tile (tile index `tile`) of the volume/update kernel.  A is read through a
 // reference so the batched kernels can pass per-instance arguments kept in device memory.
-template <int D, int N, typename R, int TT>
+// Shared memory of the volume kernel: the pointwise fluxes of the tile, then (kStage) the
+// per-thread staging slots of the RK operands (FP64 solution, FP32 stage register).
+template <int D, int N, typename R, int TT, bool kStage>
+struct VolSmem {
+  using T = Tile<D, N, TT>;
+  static constexpr size_t FLUX = sizeof(R) * T::EPB * D * T::NV * T::ND;
+  static constexpr size_t W_OFF = (FLUX + 15) / 16 * 16;
+  static constexpr size_t Q_OFF = W_OFF + sizeof(double) * T::NV * T::THREADS;
+  static constexpr size_t BYTES = kStage ? Q_OFF + sizeof(float) * T::NV * T::THREADS : FLUX;
+};
+
+// The FP32 form is bound by memory latency: it stages its stage input, solution and 2N
+// register through shared memory with asynchronous copies issued at the start, so the
+// reads of the RK update are in flight during the volume work instead of after it.
+template <typename R> struct VolStages { static constexpr bool value = false; };
+template <> struct VolStages<float> { static constexpr bool value = true; };
+
+template <int D, int N, typename R, int TT, bool kStage = false>
 __device__ __forceinline__ void vol_body(const VolArgs& A, int tile, unsigned char* smem_raw) {
   using T = Tile<D, N, TT>;
   using S = typename Arith<R>::S;
+  using SM = VolSmem<D, N, R, TT, kStage>;
   constexpr int ND = T::ND, NF = T::NF, NV = T::NV, EPB = T::EPB;
   R* sF = reinterpret_cast<R*>(smem_raw);  // [EPB][D][NV][ND]
+  double* sW = reinterpret_cast<double*>(smem_raw + SM::W_OFF);  // [NV][THREADS] (kStage)
+  float* sQ = reinterpret_cast<float*>(smem_raw + SM::Q_OFF);    // [NV][THREADS] (kStage)
   const int el = threadIdx.x / ND, node = threadIdx.x - el * ND;
   const int e0 = tile * EPB;
   const int ne = (int)A.m.ne;
@@ -372,10 +413,42 @@ __device__ __forceinline__ void vol_body(const VolArgs& A, int tile, unsigned ch
   R u[NV];
   const bool from_r = (A.mode == kMode2R && A.stage > 0);
   const S* rin = reinterpret_cast<const S*>(A.r_in);
+  const int tid = threadIdx.x;
+  if constexpr (kStage) {
+    // group 1: the stage input (FP64 solution, or the 2R register r into the q slots);
+    // group 2: the solution when the input was r, and the 2N register q
+    const bool upd = active && A.mode != kModeRHS;
+    const bool want_q = upd && A.mode == kMode2N && A.stage > 0;
+    if (active) {
 #pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    const int idx = (v * ne + e) * ND + node;
-    u[v] = !active ? R(1.0f) : (from_r ? Arith<R>::load(rin + idx) : Arith<R>::from_double(A.w_in[idx]));
+      for (int v = 0; v < NV; ++v) {
+        const int idx = (v * ne + e) * ND + node;
+        if (from_r) cp_async4(sQ + v * T::THREADS + tid, rin + idx);
+        else cp_async8(sW + v * T::THREADS + tid, A.w_in + idx);
+      }
+    }
+    cp_async_commit();
+    if (upd && (from_r || want_q)) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const int idx = (v * ne + e) * ND + node;
+        if (from_r) cp_async8(sW + v * T::THREADS + tid, A.w + idx);
+        if (want_q) cp_async4(sQ + v * T::THREADS + tid, reinterpret_cast<const S*>(A.x) + idx);
+      }
+    }
+    cp_async_commit();
+    cp_async_wait<1>();
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+      u[v] = !active ? R(1.0f)
+                     : (from_r ? R(sQ[v * T::THREADS + tid])
+                               : Arith<R>::from_double(sW[v * T::THREADS + tid]));
+  } else {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const int idx = (v * ne + e) * ND + node;
+      u[v] = !active ? R(1.0f) : (from_r ? Arith<R>::load(rin + idx) : Arith<R>::from_double(A.w_in[idx]));
+    }
   }
   {
     R F[D][NV];
@@ -429,11 +502,21 @@ __device__ __forceinline__ void vol_body(const VolArgs& A, int tile, unsigned ch
   // 3. Runge-Kutta update; xnext = input of the next stage
   using C = typename TraceCompute<R>::C;
   C xnext[NV];
+  if constexpr (kStage) cp_async_wait<0>();
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     const int idx = (v * ne + e) * ND + node;
     double xd = 0.0;
-    const R xr = active ? Update<R>::apply(A, idx, acc_result(acc[v]), u[v], xd) : R(0.0f);
+    R xr = R(0.0f);
+    if (active) {
+      if constexpr (kStage) {
+        // from_r (2R, stage > 0) the q slots hold r, which the 2R update does not read
+        xr = Update<R>::apply(A, idx, acc_result(acc[v]), u[v], xd, A.mode != kModeRHS,
+                              sW[v * T::THREADS + tid], R(sQ[v * T::THREADS + tid]));
+      } else {
+        xr = Update<R>::apply(A, idx, acc_result(acc[v]), u[v], xd);
+      }
+    }
     xnext[v] = trace_value<C, R>(xd, xr);
   }
 
@@ -458,7 +541,7 @@ template <int D, int N> struct VolKernelRegs<D, N, double> {
   static constexpr int value = D == 2 ? (N == 3 ? 48 : 40) : 56;  // no spills (ptxas, sm_103a)
 };
 template <int D, int N> struct VolKernelRegs<D, N, float> {
-  static constexpr int value = (D == 2 || N == 4) ? 32 : 40;  // no spills (ptxas, sm_103a)
+  static constexpr int value = (D == 2 && N != 3 && N != 4) ? 32 : 40;  // no spills (ptxas, sm_103a)
 };
 
 template <int D, int N, typename R, int TT = 128>
@@ -467,7 +550,7 @@ __global__ void __launch_bounds__(Tile<D, N, TT>::THREADS,
                                                  Tile<D, N, TT>::THREADS))
 vol_kernel(const VolArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  vol_body<D, N, R, TT>(A, blockIdx.x, smem_raw);
+  vol_body<D, N, R, TT, VolStages<R>::value>(A, blockIdx.x, smem_raw);
 }
 
 // Random-delay draw (same definition as the host schedule).
@@ -595,7 +678,7 @@ template <int D, int N, typename R>
 cudaError_t launch_vol_t(const VolArgs& a, cudaStream_t s) {
   using T = Tile<D, N>;
   const int64_t blocks = (a.m.ne + T::EPB - 1) / T::EPB;
-  const size_t smem = sizeof(R) * T::EPB * D * T::NV * T::ND;
+  const size_t smem = VolSmem<D, N, R, 128, VolStages<R>::value>::BYTES;
   if (smem > 48 * 1024) {
     cudaError_t err = cudaFuncSetAttribute(vol_kernel<D, N, R>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
