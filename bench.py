@@ -57,14 +57,18 @@ def vol_flops_per_node(D=2, N=DEGREE + 1):
     return pointwise + sweeps + lift + rk + traces
 
 
-def vol_bytes_per_dof_stage(stage, stages=5):
-    """Algorithmic HBM bytes per DoF of one 2N stage: read w (+ q after the first stage),
-    write w (+ q before the last stage), FP64."""
+Q_BYTES = {"fp64": 8, "df64": 8, "fp32": 4}  # storage of the 2N register q per value
+
+
+def vol_bytes_per_dof_stage(stage, stages=5, qbytes=8):
+    """Algorithmic HBM bytes per DoF of one 2N stage: read and write the FP64 solution w,
+    read q after the first stage, write q before the last stage (q in the operator's
+    storage: FP64, FP32 pair or FP32)."""
     b = 16
     if stage > 0:
-        b += 8
+        b += qbytes
     if stage < stages - 1:
-        b += 8
+        b += qbytes
     return b
 
 
@@ -427,7 +431,8 @@ def run_gpu(args, rank, world, local_rank):
     vol_avg_s = vol_ms * 1e-3 / max(vol_n, 1)
     nodes = N_ELEM * N_ELEM * (DEGREE + 1) ** 2
     flops_launch = vol_flops_per_node() * nodes
-    bytes_launch = np.mean([vol_bytes_per_dof_stage(m) for m in range(5)]) * ndof
+    bytes_launch = np.mean([vol_bytes_per_dof_stage(m, 5, Q_BYTES[args.precision])
+                            for m in range(5)]) * ndof
     pk = peaks()
     fp64_peak_tflops = 1.25  # nominal GB300 FP64 rate (no FP64 tensor advantage)
     if args.precision == "fp64":

@@ -175,6 +175,24 @@ adg_status adg_l2_error_vortex(adg_solver* s, double t, double beta, double x0, 
 /* ADG_OK if every state value is finite, ADG_ERR_NONFINITE otherwise. */
 adg_status adg_check_finite(adg_solver* s);
 
+/* ---- checkpoint / resume ---------------------------------------------------------- */
+/* A checkpoint holds everything later steps depend on: the solution, the stored traces,
+ * the ring of stored subdomain-face levels with its head, the step index, time and time
+ * step.  Restoring it into a handle created with the same mesh, degree, subdomains,
+ * maximum delay, flux, RK scheme, delay mode and seed, and precision continues the run
+ * bit for bit (the delay schedule depends only on the step index and the seed).  Setting
+ * a state with adg_set_state instead restarts the schedule at step 0, with the warm-up
+ * communication steps of Algorithm 3.
+ * adg_checkpoint_bytes: size of the checkpoint of this handle.
+ * adg_checkpoint_save: waits for the stream and writes the checkpoint to the host buffer
+ *   buf (bytes >= adg_checkpoint_bytes).  ADG_ERR_STATE without a state.
+ * adg_checkpoint_restore: reads a checkpoint from host memory; ADG_ERR_INVALID if it is
+ *   truncated, not a checkpoint, or from an incompatible handle (adg_last_error says which
+ *   field differs).  The buffer is owned by the caller and not kept. */
+adg_status adg_checkpoint_bytes(const adg_solver* s, int64_t* bytes);
+adg_status adg_checkpoint_save(adg_solver* s, void* buf, int64_t bytes);
+adg_status adg_checkpoint_restore(adg_solver* s, const void* buf, int64_t bytes);
+
 /* Kernel timing.  While enabled, adg_step records a CUDA event pair on the handle's stream
  * around every kernel it launches.  adg_get_profile waits for the stream and returns, per
  * kernel kind (0: face-flux kernel, 1: volume/update kernel), the summed device time in ms

@@ -28,6 +28,7 @@ SYMBOLS = ["adg_default_options", "adg_create", "adg_set_state", "adg_init_vorte
            "adg_init_tgv", "adg_step", "adg_get_state", "adg_rhs", "adg_get_schedule",
            "adg_info", "adg_conservation", "adg_l2_error_vortex", "adg_check_finite",
            "adg_last_error", "adg_destroy", "adg_set_profiling", "adg_get_profile", "adg_rhs_noalloc",
+           "adg_checkpoint_bytes", "adg_checkpoint_save", "adg_checkpoint_restore",
            "adg_batch_create", "adg_batch_init_vortex", "adg_batch_set_state", "adg_batch_step",
            "adg_batch_autotune", "adg_batch_get_state", "adg_batch_info",
            "adg_batch_l2_error_vortex", "adg_batch_num_groups", "adg_batch_last_error",
@@ -90,6 +91,9 @@ def lib():
             "adg_set_profiling": ([P, I], I),
             "adg_get_profile": ([P, P, P], I),
             "adg_rhs_noalloc": ([ctypes.POINTER(Mesh), I, D, P, P, I64, P], I),
+            "adg_checkpoint_bytes": ([P, P], I),
+            "adg_checkpoint_save": ([P, P, I64], I),
+            "adg_checkpoint_restore": ([P, P, I64], I),
             "adg_batch_create": ([I, P, P, P, P, I, ctypes.POINTER(Options),
                                   ctypes.POINTER(ctypes.c_void_p)], I),
             "adg_batch_init_vortex": ([P, I, D, D, D], I),
@@ -345,6 +349,19 @@ class Solver:
         n = np.zeros(2, np.int64)
         self._chk(self._L.adg_get_profile(self._h, _np_ptr(ms), _np_ptr(n)))
         return {"flux": (float(ms[0]), int(n[0])), "vol": (float(ms[1]), int(n[1]))}
+
+    def checkpoint(self):
+        """The run state (see adg_checkpoint_save) as a numpy uint8 array."""
+        n = ctypes.c_int64()
+        self._chk(self._L.adg_checkpoint_bytes(self._h, ctypes.byref(n)))
+        buf = np.empty(n.value, np.uint8)
+        self._chk(self._L.adg_checkpoint_save(self._h, _np_ptr(buf), n.value))
+        return buf
+
+    def restore(self, buf):
+        """Continue from a checkpoint taken by a compatible handle."""
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        self._chk(self._L.adg_checkpoint_restore(self._h, _np_ptr(buf), buf.size))
 
     def set_learned_model(self, params_bf16, trust=1.0):
         """params_bf16: numpy uint16 array of adg_mlp_num_params() BF16 values."""

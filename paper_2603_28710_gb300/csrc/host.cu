@@ -367,6 +367,8 @@ FluxArgs base_flux_args(adg_solver* s) {
   return fa;
 }
 
+adg_status upload_dt_tables(adg_solver* s);
+
 adg_status after_state_set(adg_solver* s) {
   s->has_state = true;
   s->step = 0;
@@ -388,7 +390,16 @@ adg_status after_state_set(adg_solver* s) {
     if (s->opt.t_end > 0) dt = s->opt.t_end / std::ceil(s->opt.t_end / dt);
     s->dt = dt;
   }
-  // dt-scaled operator tables for the 2N update
+  adg_status st = upload_dt_tables(s);
+  if (st != ADG_OK) return st;
+  st = launch_traces_of(s, s->w);
+  if (st != ADG_OK) return st;
+  s->traces_valid = true;
+  return ADG_OK;
+}
+
+// dt-scaled operator tables for the 2N update, uploaded with the others
+adg_status upload_dt_tables(adg_solver* s) {
   for (int d = 0; d < 3; ++d) {
     for (int i = 0; i < s->N * s->N; ++i) {
       s->tab.Qs[d][i] = s->tab.Q[d][i] * s->dt;
@@ -402,10 +413,63 @@ adg_status after_state_set(adg_solver* s) {
     }
   }
   ADG_CUDA(s, cudaMemcpyAsync(s->tab_dev, &s->tab, sizeof(OpTables), cudaMemcpyHostToDevice, s->stream));
-  adg_status st = launch_traces_of(s, s->w);
-  if (st != ADG_OK) return st;
-  s->traces_valid = true;
   return ADG_OK;
+}
+
+// Checkpoint layout: this header, then the solution (FP64), the traces and the ring
+// (operator storage type).
+struct CkptHeader {
+  char magic[8];
+  int32_t version, dim, degree, prec, flux, rk, delay_mode, max_delay, np, depth, rdmax;
+  int32_t P[3], n_elem[3], head;
+  int64_t ndof, n_tr, n_ring, step;
+  uint64_t seed;
+  double t, dt, lo[3], hi[3], gamma;
+};
+constexpr char kCkptMagic[8] = {'A', 'D', 'G', 'C', 'K', 'P', 'T', '1'};
+
+int64_t ckpt_tr_values(const adg_solver* s) { return (int64_t)2 * s->dim * s->NV * s->ne * s->NF; }
+int64_t ckpt_ring_values(const adg_solver* s) {
+  if (!s->ring) return 0;
+  return (int64_t)s->depth * (s->flux >= ADG_FLUX_AT_TRACE ? 2 : 1) * s->NV * s->npe * s->NF;
+}
+
+CkptHeader ckpt_header(const adg_solver* s) {
+  CkptHeader h;
+  std::memset(&h, 0, sizeof(h));
+  std::memcpy(h.magic, kCkptMagic, 8);
+  h.version = 1;
+  h.dim = s->dim;
+  h.degree = s->degree;
+  h.prec = s->prec;
+  h.flux = (int32_t)s->flux;
+  h.rk = (int32_t)s->opt.rk;
+  h.delay_mode = (int32_t)s->opt.delay_mode;
+  h.max_delay = s->max_delay;
+  h.np = s->np;
+  h.depth = s->depth;
+  h.rdmax = s->opt.random_delay_max;
+  for (int d = 0; d < 3; ++d) {
+    h.P[d] = s->P[d];
+    h.n_elem[d] = s->mesh.n_elem[d];
+    h.lo[d] = s->mesh.lo[d];
+    h.hi[d] = s->mesh.hi[d];
+  }
+  h.head = s->head;
+  h.ndof = s->ndof;
+  h.n_tr = ckpt_tr_values(s);
+  h.n_ring = ckpt_ring_values(s);
+  h.step = s->step;
+  h.seed = s->opt.seed;
+  h.t = s->t;
+  h.dt = s->dt;
+  h.gamma = s->opt.gamma;
+  return h;
+}
+
+int64_t ckpt_bytes(const adg_solver* s) {
+  const int64_t sb = (int64_t)prec_bytes(s->prec);
+  return (int64_t)sizeof(CkptHeader) + s->ndof * 8 + (ckpt_tr_values(s) + ckpt_ring_values(s)) * sb;
 }
 
 }  // namespace
@@ -800,6 +864,83 @@ adg_status adg_get_state(adg_solver* s, double* u, int64_t count, int on_device)
                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                               s->stream));
   ADG_CUDA(s, cudaStreamSynchronize(s->stream));
+  return ADG_OK;
+}
+
+adg_status adg_checkpoint_bytes(const adg_solver* s, int64_t* bytes) {
+  if (!s) return fail(nullptr, ADG_ERR_INVALID, "handle is NULL");
+  if (!bytes) return fail(const_cast<adg_solver*>(s), ADG_ERR_INVALID, "bytes is NULL");
+  *bytes = ckpt_bytes(s);
+  return ADG_OK;
+}
+
+adg_status adg_checkpoint_save(adg_solver* s, void* buf, int64_t bytes) {
+  if (!s) return fail(nullptr, ADG_ERR_INVALID, "handle is NULL");
+  if (!buf) return fail(s, ADG_ERR_INVALID, "buf is NULL");
+  if (bytes < ckpt_bytes(s)) return fail(s, ADG_ERR_INVALID, "buffer smaller than adg_checkpoint_bytes");
+  if (!s->has_state) return fail(s, ADG_ERR_STATE, "no state to checkpoint");
+  if (!s->traces_valid) {
+    adg_status st = launch_traces_of(s, s->w);
+    if (st != ADG_OK) return st;
+    s->traces_valid = true;
+  }
+  const CkptHeader h = ckpt_header(s);
+  unsigned char* p = static_cast<unsigned char*>(buf);
+  std::memcpy(p, &h, sizeof(h));
+  p += sizeof(h);
+  const size_t sb = prec_bytes(s->prec);
+  ADG_CUDA(s, cudaMemcpyAsync(p, s->w, (size_t)h.ndof * 8, cudaMemcpyDeviceToHost, s->stream));
+  p += (size_t)h.ndof * 8;
+  ADG_CUDA(s, cudaMemcpyAsync(p, s->tr, (size_t)h.n_tr * sb, cudaMemcpyDeviceToHost, s->stream));
+  p += (size_t)h.n_tr * sb;
+  if (h.n_ring > 0)
+    ADG_CUDA(s, cudaMemcpyAsync(p, s->ring, (size_t)h.n_ring * sb, cudaMemcpyDeviceToHost, s->stream));
+  ADG_CUDA(s, cudaStreamSynchronize(s->stream));
+  return ADG_OK;
+}
+
+adg_status adg_checkpoint_restore(adg_solver* s, const void* buf, int64_t bytes) {
+  if (!s) return fail(nullptr, ADG_ERR_INVALID, "handle is NULL");
+  if (!buf) return fail(s, ADG_ERR_INVALID, "buf is NULL");
+  if (bytes < (int64_t)sizeof(CkptHeader)) return fail(s, ADG_ERR_INVALID, "checkpoint truncated");
+  CkptHeader h;
+  std::memcpy(&h, buf, sizeof(h));
+  if (std::memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != 1)
+    return fail(s, ADG_ERR_INVALID, "not an ADG checkpoint (version 1)");
+  const CkptHeader m = ckpt_header(s);
+  struct { const char* name; bool same; } fields[] = {
+      {"dim", h.dim == m.dim}, {"degree", h.degree == m.degree}, {"precision", h.prec == m.prec},
+      {"flux", h.flux == m.flux}, {"rk", h.rk == m.rk}, {"delay_mode", h.delay_mode == m.delay_mode},
+      {"max_delay", h.max_delay == m.max_delay}, {"at_np", h.np == m.np},
+      {"random_delay_max", h.rdmax == m.rdmax}, {"seed", h.seed == m.seed},
+      {"gamma", h.gamma == m.gamma},
+      {"P", h.P[0] == m.P[0] && h.P[1] == m.P[1] && h.P[2] == m.P[2]},
+      {"mesh", h.n_elem[0] == m.n_elem[0] && h.n_elem[1] == m.n_elem[1] && h.n_elem[2] == m.n_elem[2] &&
+                   h.lo[0] == m.lo[0] && h.lo[1] == m.lo[1] && h.lo[2] == m.lo[2] &&
+                   h.hi[0] == m.hi[0] && h.hi[1] == m.hi[1] && h.hi[2] == m.hi[2]},
+      {"sizes", h.ndof == m.ndof && h.n_tr == m.n_tr && h.n_ring == m.n_ring && h.depth == m.depth}};
+  for (const auto& f : fields)
+    if (!f.same) return fail(s, ADG_ERR_INVALID, std::string("checkpoint from an incompatible handle: ") + f.name);
+  if (bytes < ckpt_bytes(s)) return fail(s, ADG_ERR_INVALID, "checkpoint truncated");
+  if (!(h.dt > 0) || !std::isfinite(h.dt) || h.step < 0 || h.head < -1 || h.head >= (h.depth > 0 ? h.depth : 1))
+    return fail(s, ADG_ERR_INVALID, "checkpoint has an invalid step, head or time step");
+  const unsigned char* p = static_cast<const unsigned char*>(buf) + sizeof(h);
+  const size_t sb = prec_bytes(s->prec);
+  ADG_CUDA(s, cudaMemcpyAsync(s->w, p, (size_t)h.ndof * 8, cudaMemcpyHostToDevice, s->stream));
+  p += (size_t)h.ndof * 8;
+  ADG_CUDA(s, cudaMemcpyAsync(s->tr, p, (size_t)h.n_tr * sb, cudaMemcpyHostToDevice, s->stream));
+  p += (size_t)h.n_tr * sb;
+  if (h.n_ring > 0)
+    ADG_CUDA(s, cudaMemcpyAsync(s->ring, p, (size_t)h.n_ring * sb, cudaMemcpyHostToDevice, s->stream));
+  s->dt = h.dt;
+  adg_status st = upload_dt_tables(s);
+  if (st != ADG_OK) return st;
+  ADG_CUDA(s, cudaStreamSynchronize(s->stream));  // the caller's buffer is not kept
+  s->has_state = true;
+  s->traces_valid = true;
+  s->step = h.step;
+  s->t = h.t;
+  s->head = h.head;
   return ADG_OK;
 }
 
