@@ -117,3 +117,44 @@ def test_fp32_error_bounded():
     drift = np.abs(c - c0).max() / np.abs(c0).max()
     print(f"fp32 operator: conservation drift after 50 steps {drift:.2e}")
     assert drift < 1e-7
+
+
+@pytest.mark.parametrize("flux,mode,rk", [("at", "caa", "rk22"), ("at", "caa", "rk33"),
+                                          ("std", "caa", "ck45"), ("at_trace", "random", "ck45"),
+                                          ("at", "random", "rk33")])
+def test_fp32_steps_every_scheme(flux, mode, rk):
+    # every update form of the FP32 volume kernel (2R stage 0 / later stages, 2N) and its
+    # staged operands against the FP64 oracle
+    kw = dict(P=(4, 4), max_delay=3, flux=flux, rk=rk, delay_mode=mode, random_delay_max=2,
+              seed=99)
+    o0 = O.Oracle(n_elem=(16, 12), degree=3, dt=1.0)
+    u0 = o0.init_vortex()
+    dt = o0.dt_from_cfl(u0, 0.1, 0.0)
+    s = adg.Solver(n_elem=(16, 12), degree=3, precision="fp32", dt=dt, **kw)
+    o = O.Oracle(n_elem=(16, 12), degree=3, dt=dt, **kw)
+    s.set_state(u0)
+    o.set_state(u0)
+    s.step(1)
+    o.step(1)
+    e1 = rel(s.get_state(), o.get_state())
+    s.step(19)
+    o.step(19)
+    e20 = rel(s.get_state(), o.get_state())
+    print(f"fp32 {flux}/{mode}/{rk}: relative L2 error after 1 step {e1:.2e}, after 20 {e20:.2e}")
+    assert e1 < 2e-8
+    assert e20 < 5e-7
+
+
+@pytest.mark.parametrize("dim,n_elem,p", [(2, (5, 3), 2), (2, (7, 4), 5), (3, (3, 2, 2), 3)])
+def test_fp32_rhs_random_state(dim, n_elem, p):
+    # adg_rhs in the FP32 operator: the output as an increment over a CFL-limited step
+    lo, hi = (-5.0,) * dim, (5.0,) * dim
+    s = adg.Solver(dim=dim, n_elem=n_elem, degree=p, lo=lo, hi=hi, dt=1e-3, precision="fp32")
+    o = O.Oracle(dim=dim, n_elem=n_elem, degree=p, lo=lo, hi=hi, dt=1e-3)
+    u = random_state(s.shape, dim, seed=31 + p)
+    kg = s.rhs(u)
+    ko = o.rhs(u)
+    dt = o.dt_from_cfl(u, 0.1, 0.0)
+    inc = np.linalg.norm((kg - ko) * dt) / np.linalg.norm(u)
+    print(f"fp32 rhs {dim}D p={p}: increment error {inc:.2e}")
+    assert inc < 1e-7
