@@ -78,18 +78,18 @@ struct Arith<df64> {
   __device__ static __forceinline__ df64 pair(double, float2 f) { return df64(f.x, f.y); }
 };
 
-// FP64 reciprocal: an FP32 seed (integer conversions, MUFU approximation, relative error
-// about 2^-22) refined by two Newton-Raphson steps r <- r + r (1 - x r), each squaring the
-// error: about 2^-44, then below FP64 rounding.  4 DFMA instead of the IEEE division
-// sequence; not correctly rounded (within an ulp).  For 1e-37 < |x| < 1e37.
+// FP64 reciprocal: an FP32 seed r0 (integer conversions, MUFU approximation, relative
+// error |e| about 2^-22 with e = 1 - x r0) refined by the geometric series
+// 1/x = r0 / (1 - e) = r0 (1 + e + e^2 + ...), kept to second order: the truncation leaves
+// e^3 (about 2^-66), below FP64 rounding.  3 DFMA instead of the IEEE division sequence;
+// not correctly rounded (within an ulp).  For 1e-37 < |x| < 1e37.
 __device__ __forceinline__ double r_rcp(double x) {
   float xf = d2f_int(x), rf;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(xf));
-  double r = f2d_int(rf);
-  double e = fma(-x, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-x, r, 1.0);
-  return fma(r, e, r);
+  const double r0 = f2d_int(rf);
+  const double e = fma(-x, r0, 1.0);
+  const double p = fma(e, e, e);  // e + e^2
+  return fma(r0, p, r0);
 }
 // FP32 operator: the hardware approximations (PTX rcp.approx / sqrt.approx, at most one
 // ulp and 2^-23 relative error), one instruction each instead of the IEEE sequences.
