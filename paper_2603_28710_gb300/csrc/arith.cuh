@@ -109,6 +109,15 @@ __device__ __forceinline__ float r_max(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ double r_fma(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float r_fma(float a, float b, float c) { return fmaf(a, b, c); }
 
+// w - k / 2 (one fused operation where the arithmetic has one)
+__device__ __forceinline__ double sub_half(double w, double k) { return fma(-0.5, k, w); }
+__device__ __forceinline__ float sub_half(float w, float k) { return fmaf(-0.5f, k, w); }
+__device__ __forceinline__ df64 sub_half(df64 w, df64 k) { return w - df64(0.5f * k.hi, 0.5f * k.lo); }
+
+// multiplication by a power of two (exact)
+__device__ __forceinline__ double scale_pow2(double x, float p2) { return x * (double)p2; }
+__device__ __forceinline__ float scale_pow2(float x, float p2) { return x * p2; }
+
 // exact halving
 __device__ __forceinline__ double half(double x) { return 0.5 * x; }
 __device__ __forceinline__ float half(float x) { return 0.5f * x; }

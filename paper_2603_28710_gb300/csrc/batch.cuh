@@ -66,9 +66,10 @@ __device__ __forceinline__ void stage_args(T* dst, const T* src) {
 // 48 against 32 at 128 threads, over 90 for tiles of 64 threads when left to the
 // compiler), which cuts the occupancy the latency-bound FP32 form needs.  Budgets without
 // spills (ptxas, sm_103a): FP32 40 registers in 2D (48 at N = 4 and 8 and for tiles of at
-// most 64 threads), 56 in 3D; FP64 and FP32 pairs 16 above the single-instance budget.
+// most 64 threads), 56 in 3D; FP64 and FP32 pairs 16 above the single-instance budget
+// (24 at N = 8).
 template <int D, int N, typename R> struct VolRegs {
-  static constexpr int value = VolKernelRegs<D, N, R>::value + 16;
+  static constexpr int value = VolKernelRegs<D, N, R>::value + (N == 8 ? 24 : 16);
 };
 template <int D, int N> struct VolRegs<D, N, float> {
   static constexpr int value = D != 2 ? 56 : ((N == 4 || N == 8) ? 48 : 40);

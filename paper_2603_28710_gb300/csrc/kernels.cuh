@@ -100,19 +100,18 @@ template <int D, typename R>
 __device__ __forceinline__ void side_flux(const R (&w)[D + 2], int d, R gamma, R gm1,
                                           R (&fd)[D + 2], R& s2) {
   const R irho = r_rcp(w[0]);
-  R u2 = R(0.0f), kin2 = R(0.0f), ud = R(0.0f), md = w[1];
+  R u2 = R(0.0f), ud = R(0.0f), md = w[1];
 #pragma unroll
   for (int c = 0; c < D; ++c) {
     const R uc = w[1 + c] * irho;
     u2 = r_fma(uc, uc, u2);
-    kin2 = r_fma(w[1 + c], uc, kin2);
     if (c == d) {
       ud = uc;
       md = w[1 + c];
     }
   }
-  const R p = gm1 * (w[D + 1] - R(0.5f) * kin2);
-  s2 = u2 + gamma * p * irho;
+  const R p = gm1 * sub_half(w[D + 1], w[0] * u2);  // (gamma - 1) (E - rho |u|^2 / 2)
+  s2 = r_fma(gamma * p, irho, u2);                  // |u|^2 + gamma p / rho
   fd[0] = md;
 #pragma unroll
   for (int c = 0; c < D; ++c) {
@@ -131,8 +130,7 @@ __device__ __forceinline__ void llf_flux(const R (&wm)[D + 2], const R (&wp)[D +
   R fm[NV], fp[NV], sm, sp;
   side_flux<D, R>(wm, d, gamma, gm1, fm, sm);
   side_flux<D, R>(wp, d, gamma, gm1, fp, sp);
-  const R lam = R(0.5f) * r_sqrt(r_max(sm, sp));
-  const R hl = R(0.5f) * lam;
+  const R hl = scale_pow2(r_sqrt(r_max(sm, sp)), 0.25f);  // lambda / 2, lambda = sqrt(max) / 2
 #pragma unroll
   for (int v = 0; v < NV; ++v) f[v] = R(0.5f) * (fm[v] + fp[v]) + hl * (wm[v] - wp[v]);
 }
@@ -538,7 +536,7 @@ template <int D, int N, typename R> struct VolKernelRegs {
   static constexpr int value = D == 2 ? 48 : 56;
 };
 template <int D, int N> struct VolKernelRegs<D, N, double> {
-  static constexpr int value = D == 2 ? (N == 3 ? 48 : 40) : 56;  // no spills (ptxas, sm_103a)
+  static constexpr int value = D == 2 ? ((N == 3 || N == 8) ? 48 : 40) : 56;  // no spills (ptxas)
 };
 template <int D, int N> struct VolKernelRegs<D, N, float> {
   static constexpr int value = (D == 2 && N != 3 && N != 4) ? 32 : 40;  // no spills (ptxas, sm_103a)
@@ -651,7 +649,7 @@ __device__ __forceinline__ void flux_body(const FluxArgs& A, int bx, int d) {
 }
 
 // Register budget of the face-flux kernel (blocks of 256 threads; no spills, ptxas sm_103a).
-template <int D, typename R> struct FluxKernelRegs { static constexpr int value = 64; };
+template <int D, typename R> struct FluxKernelRegs { static constexpr int value = D == 2 ? 64 : 72; };
 template <int D> struct FluxKernelRegs<D, float> { static constexpr int value = 48; };
 template <int D> struct FluxKernelRegs<D, df64> { static constexpr int value = D == 2 ? 48 : 64; };
 
