@@ -82,13 +82,14 @@ __device__ __forceinline__ void euler_flux_all(const R (&w)[D + 2], R gm1, R (&F
     kacc = acc_fma(w[1 + d], u[d], kacc);
   }
   const R kin2 = acc_result(kacc);
-  const R p = gm1 * (w[D + 1] - half(kin2));
+  const R p = gm1 * sub_half(w[D + 1], kin2);
   const R ep = w[D + 1] + p;
 #pragma unroll
   for (int d = 0; d < D; ++d) {
     F[d][0] = w[1 + d];
 #pragma unroll
-    for (int c = 0; c < D; ++c) F[d][1 + c] = w[1 + c] * u[d];
+    for (int c = 0; c < D; ++c)  // rho u_c u_d is symmetric: each product once
+      F[d][1 + c] = c < d ? F[c][1 + d] : w[1 + c] * u[d];
     F[d][1 + d] = F[d][1 + d] + p;
     F[d][D + 1] = ep * u[d];
   }
