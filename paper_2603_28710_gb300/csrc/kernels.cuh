@@ -380,14 +380,24 @@ struct VolSmem {
   static constexpr size_t FLUX = sizeof(R) * T::EPB * D * T::NV * T::ND;
   static constexpr size_t W_OFF = (FLUX + 15) / 16 * 16;
   static constexpr size_t Q_OFF = W_OFF + sizeof(double) * T::NV * T::THREADS;
-  static constexpr size_t BYTES = kStage ? Q_OFF + sizeof(float) * T::NV * T::THREADS : FLUX;
+  static constexpr size_t BYTES =
+      kStage ? Q_OFF + sizeof(typename Arith<R>::S) * T::NV * T::THREADS : FLUX;
 };
 
-// The FP32 form is bound by memory latency: it stages its stage input, solution and 2N
-// register through shared memory with asynchronous copies issued at the start, so the
-// reads of the RK update are in flight during the volume work instead of after it.
+// The FP32 and FP32-pair forms wait on memory more than on their pipes: they stage their
+// stage input, solution and 2N register through shared memory with asynchronous copies
+// issued at the start, so the reads of the RK update are in flight during the volume work
+// instead of after it (512^2 p=4: FP32 210 -> 187 us, pairs 8 % faster).  The FP64 form is
+// bound by its FP64 pipe and keeps plain loads.
 template <typename R> struct VolStages { static constexpr bool value = false; };
 template <> struct VolStages<float> { static constexpr bool value = true; };
+template <> struct VolStages<df64> { static constexpr bool value = true; };
+
+// asynchronous copy of one stored value (FP32: 4 bytes, FP32 pair: 8 bytes)
+__device__ __forceinline__ void cp_async_val(float* smem, const float* gmem) { cp_async4(smem, gmem); }
+__device__ __forceinline__ void cp_async_val(float2* smem, const float2* gmem) { cp_async8(smem, gmem); }
+__device__ __forceinline__ float from_stored(float v) { return v; }
+__device__ __forceinline__ df64 from_stored(float2 v) { return df64(v.x, v.y); }
 
 template <int D, int N, typename R, int TT, bool kStage = false>
 __device__ __forceinline__ void vol_body(const VolArgs& A, int tile, unsigned char* smem_raw) {
@@ -397,7 +407,7 @@ __device__ __forceinline__ void vol_body(const VolArgs& A, int tile, unsigned ch
   constexpr int ND = T::ND, NF = T::NF, NV = T::NV, EPB = T::EPB;
   R* sF = reinterpret_cast<R*>(smem_raw);  // [EPB][D][NV][ND]
   double* sW = reinterpret_cast<double*>(smem_raw + SM::W_OFF);  // [NV][THREADS] (kStage)
-  float* sQ = reinterpret_cast<float*>(smem_raw + SM::Q_OFF);    // [NV][THREADS] (kStage)
+  S* sQ = reinterpret_cast<S*>(smem_raw + SM::Q_OFF);            // [NV][THREADS] (kStage)
   const int el = threadIdx.x / ND, node = threadIdx.x - el * ND;
   const int e0 = tile * EPB;
   const int ne = (int)A.m.ne;
@@ -422,7 +432,7 @@ __device__ __forceinline__ void vol_body(const VolArgs& A, int tile, unsigned ch
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         const int idx = (v * ne + e) * ND + node;
-        if (from_r) cp_async4(sQ + v * T::THREADS + tid, rin + idx);
+        if (from_r) cp_async_val(sQ + v * T::THREADS + tid, rin + idx);
         else cp_async8(sW + v * T::THREADS + tid, A.w_in + idx);
       }
     }
@@ -432,7 +442,7 @@ __device__ __forceinline__ void vol_body(const VolArgs& A, int tile, unsigned ch
       for (int v = 0; v < NV; ++v) {
         const int idx = (v * ne + e) * ND + node;
         if (from_r) cp_async8(sW + v * T::THREADS + tid, A.w + idx);
-        if (want_q) cp_async4(sQ + v * T::THREADS + tid, reinterpret_cast<const S*>(A.x) + idx);
+        if (want_q) cp_async_val(sQ + v * T::THREADS + tid, reinterpret_cast<const S*>(A.x) + idx);
       }
     }
     cp_async_commit();
@@ -440,7 +450,7 @@ __device__ __forceinline__ void vol_body(const VolArgs& A, int tile, unsigned ch
 #pragma unroll
     for (int v = 0; v < NV; ++v)
       u[v] = !active ? R(1.0f)
-                     : (from_r ? R(sQ[v * T::THREADS + tid])
+                     : (from_r ? from_stored(sQ[v * T::THREADS + tid])
                                : Arith<R>::from_double(sW[v * T::THREADS + tid]));
   } else {
 #pragma unroll
@@ -511,7 +521,7 @@ __device__ __forceinline__ void vol_body(const VolArgs& A, int tile, unsigned ch
       if constexpr (kStage) {
         // from_r (2R, stage > 0) the q slots hold r, which the 2R update does not read
         xr = Update<R>::apply(A, idx, acc_result(acc[v]), u[v], xd, A.mode != kModeRHS,
-                              sW[v * T::THREADS + tid], R(sQ[v * T::THREADS + tid]));
+                              sW[v * T::THREADS + tid], from_stored(sQ[v * T::THREADS + tid]));
       } else {
         xr = Update<R>::apply(A, idx, acc_result(acc[v]), u[v], xd);
       }
