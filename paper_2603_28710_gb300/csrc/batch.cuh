@@ -128,7 +128,7 @@ struct BatchDispatch {
   static cudaError_t vol_t(const VolArgs* va, int ns, int st, const BatchGroupArgs& g, int grid,
                            cudaStream_t s, int* occ) {
     using T = Tile<D, N, TT>;
-    const size_t smem = sizeof(R) * T::EPB * D * T::NV * T::ND;
+    const size_t smem = vol_flux_bytes<D, N, R, TT>();
     if (smem > 48 * 1024) {
       cudaError_t e = cudaFuncSetAttribute(batch_vol_kernel<D, N, R, TT>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

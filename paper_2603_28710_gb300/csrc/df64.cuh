@@ -151,4 +151,38 @@ __device__ __forceinline__ df64 acc_result(df64acc t) {
   return df64(zh, zl);
 }
 
+// Two compensated dot products advanced together with the packed FP32x2 instructions of
+// sm_100 and later (FFMA2 / FADD2 / FMUL2: two independent, correctly rounded FP32
+// operations per instruction): lane k of every float2 belongs to the k-th dot product.
+// Lane by lane the operation sequence of acc_fma (its subtractions written as fused
+// multiply-adds by -1 and as negated sums, which round the same way), with half the
+// instructions.
+struct df64acc2 {
+  float2 s, c;
+};
+__device__ __forceinline__ df64acc2 acc2_zero() {
+  return df64acc2{make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
+}
+// t + a * (fh + fl) lane-wise, a = (ah, al) one pair shared by both lanes, nah = -ah
+__device__ __forceinline__ df64acc2 acc2_fma(float2 ah, float2 al, float2 nah, float2 fh,
+                                             float2 fl, df64acc2 t) {
+  const float2 m1 = make_float2(-1.0f, -1.0f);
+  const float2 pn = __fmul2_rn(nah, fh);      // -p, p = ah fh rounded
+  const float2 pe = __ffma2_rn(ah, fh, pn);   // ah fh - p, exact
+  const float2 s = __ffma2_rn(pn, m1, t.s);   // t.s + p
+  const float2 bp = __ffma2_rn(t.s, m1, s);   // s - t.s
+  const float2 ap = __ffma2_rn(bp, m1, s);    // s - bp
+  const float2 e1 = __ffma2_rn(ap, m1, t.s);  // t.s - ap
+  const float2 e2n = __fadd2_rn(pn, bp);      // -(p - bp)
+  const float2 se = __ffma2_rn(e2n, m1, e1);  // (t.s - ap) + (p - bp): the TwoSum error
+  float2 c = __fadd2_rn(t.c, __fadd2_rn(se, pe));
+  c = __ffma2_rn(ah, fl, c);
+  c = __ffma2_rn(al, fh, c);
+  return df64acc2{s, c};
+}
+// lane k as a scalar accumulator
+__device__ __forceinline__ df64acc acc2_lane(const df64acc2& t, int k) {
+  return k == 0 ? df64acc{t.s.x, t.c.x} : df64acc{t.s.y, t.c.y};
+}
+
 }  // namespace adg

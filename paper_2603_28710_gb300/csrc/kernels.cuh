@@ -374,10 +374,23 @@ struct Update<double> {
 // reference so the batched kernels can pass per-instance arguments kept in device memory.
 // Shared memory of the volume kernel: the pointwise fluxes of the tile, then (kStage) the
 // per-thread staging slots of the RK operands (FP64 solution, FP32 stage register).
+// Pointwise fluxes of a tile in shared memory: [EPB][D][NV][ND] values of R, except for
+// the 2D FP32 pairs, which keep pairs of variables together for the packed sweeps:
+// [EPB][D][NV/2][ND] of float4 {hi_v, hi_v+1, lo_v, lo_v+1}.  (In 3D the odd variable
+// count and the larger tiles cost more registers than the packing saves.)
+template <int D, typename R> struct PackedSweeps { static constexpr bool value = false; };
+template <> struct PackedSweeps<2, df64> { static constexpr bool value = true; };
+template <int D, int N, typename R, int TT>
+constexpr size_t vol_flux_bytes() {
+  using T = Tile<D, N, TT>;
+  return PackedSweeps<D, R>::value ? sizeof(float4) * T::EPB * D * ((T::NV + 1) / 2) * T::ND
+                                   : sizeof(R) * T::EPB * D * T::NV * T::ND;
+}
+
 template <int D, int N, typename R, int TT, bool kStage>
 struct VolSmem {
   using T = Tile<D, N, TT>;
-  static constexpr size_t FLUX = sizeof(R) * T::EPB * D * T::NV * T::ND;
+  static constexpr size_t FLUX = vol_flux_bytes<D, N, R, TT>();
   static constexpr size_t W_OFF = (FLUX + 15) / 16 * 16;
   static constexpr size_t Q_OFF = W_OFF + sizeof(double) * T::NV * T::THREADS;
   static constexpr size_t BYTES =
@@ -459,13 +472,26 @@ __device__ __forceinline__ void vol_body(const VolArgs& A, int tile, unsigned ch
       u[v] = !active ? R(1.0f) : (from_r ? Arith<R>::load(rin + idx) : Arith<R>::from_double(A.w_in[idx]));
     }
   }
+  constexpr int NP = (NV + 1) / 2;  // variable pairs of the packed sweeps
+  float4* sF4 = reinterpret_cast<float4*>(smem_raw);  // [EPB][D][NP][ND] (packed sweeps)
   {
     R F[D][NV];
     euler_flux_all<D, R>(u, Arith<R>::pair(A.gamma, A.gammaf) - R(1.0f), F);
+    if constexpr (PackedSweeps<D, R>::value) {
 #pragma unroll
-    for (int d = 0; d < D; ++d)
+      for (int d = 0; d < D; ++d)
 #pragma unroll
-      for (int v = 0; v < NV; ++v) sF[((el * D + d) * NV + v) * ND + node] = F[d][v];
+        for (int pr = 0; pr < NP; ++pr) {
+          const R f0 = F[d][2 * pr];
+          const R f1 = 2 * pr + 1 < NV ? F[d][2 * pr + 1] : R(0.0f);
+          sF4[((el * D + d) * NP + pr) * ND + node] = make_float4(f0.hi, f1.hi, f0.lo, f1.lo);
+        }
+    } else {
+#pragma unroll
+      for (int d = 0; d < D; ++d)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) sF[((el * D + d) * NV + v) * ND + node] = F[d][v];
+    }
   }
   __syncthreads();
 
@@ -476,19 +502,40 @@ __device__ __forceinline__ void vol_body(const VolArgs& A, int tile, unsigned ch
   for (int v = 0; v < NV; ++v) acc[v] = acc_zero(Acc());
   const S* fl = reinterpret_cast<const S*>(A.fl);
   if (active) {
+    df64acc2 acc2[NP];  // packed sweeps: lane k of pair pr accumulates variable 2 pr + k
+#pragma unroll
+    for (int pr = 0; pr < NP; ++pr) acc2[pr] = acc2_zero();
 #pragma unroll
     for (int d = 0; d < D; ++d) {
       const int stride = d == 0 ? 1 : (d == 1 ? N : N * N);
       const int base = node - ix[d] * stride;
       const double* Qd = (A.scaled ? A.tab->Qs[d] : A.tab->Q[d]) + ix[d] * N;
       const float2* Qdf = (A.scaled ? A.tab->Qsf[d] : A.tab->Qf[d]) + ix[d] * N;
+      if constexpr (PackedSweeps<D, R>::value) {
 #pragma unroll
-      for (int a = 0; a < N; ++a) {
-        const R q = Arith<R>::tab(Qd, Qdf, a);
+        for (int a = 0; a < N; ++a) {
+          const float2 q = Qdf[a];
+          const float2 qh = make_float2(q.x, q.x), ql = make_float2(q.y, q.y);
+          const float2 nqh = make_float2(-q.x, -q.x);
 #pragma unroll
-        for (int v = 0; v < NV; ++v)
-          acc[v] = acc_fma(q, sF[((el * D + d) * NV + v) * ND + base + a * stride], acc[v]);
+          for (int pr = 0; pr < NP; ++pr) {
+            const float4 f = sF4[((el * D + d) * NP + pr) * ND + base + a * stride];
+            acc2[pr] = acc2_fma(qh, ql, nqh, make_float2(f.x, f.y), make_float2(f.z, f.w), acc2[pr]);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int a = 0; a < N; ++a) {
+          const R q = Arith<R>::tab(Qd, Qdf, a);
+#pragma unroll
+          for (int v = 0; v < NV; ++v)
+            acc[v] = acc_fma(q, sF[((el * D + d) * NV + v) * ND + base + a * stride], acc[v]);
+        }
       }
+    }
+    if constexpr (PackedSweeps<D, R>::value) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) acc[v] = acc2_lane(acc2[v / 2], v & 1);
     }
 #pragma unroll
     for (int d = 0; d < D; ++d) {
@@ -544,7 +591,7 @@ __device__ __forceinline__ void vol_body(const VolArgs& A, int tile, unsigned ch
 // compiler from trading occupancy for registers).  The FP32 form is latency-bound and
 // wants every warp slot.
 template <int D, int N, typename R> struct VolKernelRegs {
-  static constexpr int value = D == 2 ? 48 : 56;
+  static constexpr int value = (D == 2 && (N == 2 || N == 8)) ? 64 : 56;  // no spills (ptxas)
 };
 template <int D, int N> struct VolKernelRegs<D, N, double> {
   static constexpr int value = D == 2 ? ((N == 3 || N == 8) ? 48 : 40) : 56;  // no spills (ptxas)
