@@ -185,4 +185,72 @@ __device__ __forceinline__ df64acc acc2_lane(const df64acc2& t, int k) {
   return k == 0 ? df64acc{t.s.x, t.c.x} : df64acc{t.s.y, t.c.y};
 }
 
+// Two independent double-word values in the lanes of float2 words (lane k: hi.k + lo.k),
+// with the scalar algorithms above executed lane-wise by the packed FP32x2 instructions:
+// the two sides of a face run their pointwise flux in one instruction stream.
+struct df64x2 {
+  float2 hi, lo;
+  __device__ __forceinline__ df64x2() {}
+  __device__ __forceinline__ df64x2(float2 h, float2 l) : hi(h), lo(l) {}
+  __device__ __forceinline__ explicit df64x2(float h)
+      : hi(make_float2(h, h)), lo(make_float2(0.0f, 0.0f)) {}
+};
+__device__ __forceinline__ df64x2 df64x2_of(df64 a, df64 b) {
+  return df64x2(make_float2(a.hi, b.hi), make_float2(a.lo, b.lo));
+}
+__device__ __forceinline__ df64 df64x2_lane(const df64x2& x, int k) {
+  return k == 0 ? df64(x.hi.x, x.lo.x) : df64(x.hi.y, x.lo.y);
+}
+
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2& s, float2& e) {
+  const float2 m1 = make_float2(-1.0f, -1.0f);
+  s = __fadd2_rn(a, b);
+  const float2 bp = __ffma2_rn(a, m1, s);   // s - a
+  const float2 ap = __ffma2_rn(bp, m1, s);  // s - bp
+  e = __fadd2_rn(__ffma2_rn(ap, m1, a), __ffma2_rn(bp, m1, b));  // (a - ap) + (b - bp)
+}
+__device__ __forceinline__ void fast_two_sum2(float2 a, float2 b, float2& s, float2& e) {
+  const float2 m1 = make_float2(-1.0f, -1.0f);
+  s = __fadd2_rn(a, b);
+  e = __ffma2_rn(__ffma2_rn(a, m1, s), m1, b);  // b - (s - a)
+}
+__device__ __forceinline__ df64x2 operator+(df64x2 x, df64x2 y) {
+  float2 sh, sl, th, tl, vh, vl, zh, zl;
+  two_sum2(x.hi, y.hi, sh, sl);
+  two_sum2(x.lo, y.lo, th, tl);
+  const float2 c = __fadd2_rn(sl, th);
+  fast_two_sum2(sh, c, vh, vl);
+  const float2 w = __fadd2_rn(tl, vl);
+  fast_two_sum2(vh, w, zh, zl);
+  return df64x2(zh, zl);
+}
+__device__ __forceinline__ df64x2 operator-(df64x2 x) { return df64x2(neg2(x.hi), neg2(x.lo)); }
+__device__ __forceinline__ df64x2 operator-(df64x2 x, df64x2 y) { return x + (-y); }
+__device__ __forceinline__ df64x2 operator*(df64x2 x, df64x2 y) {
+  const float2 ch = __fmul2_rn(x.hi, y.hi);
+  const float2 cl1 = __ffma2_rn(x.hi, y.hi, neg2(ch));  // exact product error
+  const float2 tl0 = __fmul2_rn(x.lo, y.lo);
+  const float2 tl1 = __ffma2_rn(x.hi, y.lo, tl0);
+  const float2 cl2 = __ffma2_rn(x.lo, y.hi, tl1);
+  const float2 cl3 = __fadd2_rn(cl1, cl2);
+  float2 zh, zl;
+  fast_two_sum2(ch, cl3, zh, zl);
+  return df64x2(zh, zl);
+}
+__device__ __forceinline__ df64x2 r_fma(df64x2 a, df64x2 b, df64x2 c) { return a * b + c; }
+__device__ __forceinline__ df64x2 r_rcp(df64x2 y) {
+  // per lane: FP32 seed, then the pair Newton step of r_rcp(df64)
+  const float2 r0 = make_float2(__frcp_rn(y.hi.x), __frcp_rn(y.hi.y));
+  float2 e = __ffma2_rn(neg2(y.hi), r0, make_float2(1.0f, 1.0f));
+  e = __ffma2_rn(neg2(y.lo), r0, e);
+  float2 zh, zl;
+  fast_two_sum2(r0, __fmul2_rn(r0, e), zh, zl);
+  return df64x2(zh, zl);
+}
+__device__ __forceinline__ df64x2 sub_half(df64x2 w, df64x2 k) {
+  const float2 h = make_float2(0.5f, 0.5f);
+  return w - df64x2(__fmul2_rn(h, k.hi), __fmul2_rn(h, k.lo));
+}
+
 }  // namespace adg

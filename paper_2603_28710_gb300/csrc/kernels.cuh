@@ -129,8 +129,23 @@ __device__ __forceinline__ void llf_flux(const R (&wm)[D + 2], const R (&wp)[D +
   constexpr int NV = D + 2;
   const R gm1 = gamma - R(1.0f);
   R fm[NV], fp[NV], sm, sp;
-  side_flux<D, R>(wm, d, gamma, gm1, fm, sm);
-  side_flux<D, R>(wp, d, gamma, gm1, fp, sp);
+  if constexpr (std::is_same<R, df64>::value) {
+    // FP32 pairs: both sides in the two lanes of packed FP32x2 instructions
+    df64x2 w2[NV], f2[NV], s2;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) w2[v] = df64x2_of(wm[v], wp[v]);
+    side_flux<D, df64x2>(w2, d, df64x2_of(gamma, gamma), df64x2_of(gm1, gm1), f2, s2);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      fm[v] = df64x2_lane(f2[v], 0);
+      fp[v] = df64x2_lane(f2[v], 1);
+    }
+    sm = df64x2_lane(s2, 0);
+    sp = df64x2_lane(s2, 1);
+  } else {
+    side_flux<D, R>(wm, d, gamma, gm1, fm, sm);
+    side_flux<D, R>(wp, d, gamma, gm1, fp, sp);
+  }
   const R hl = scale_pow2(r_sqrt(r_max(sm, sp)), 0.25f);  // lambda / 2, lambda = sqrt(max) / 2
 #pragma unroll
   for (int v = 0; v < NV; ++v) f[v] = R(0.5f) * (fm[v] + fp[v]) + hl * (wm[v] - wp[v]);
@@ -709,7 +724,7 @@ __device__ __forceinline__ void flux_body(const FluxArgs& A, int bx, int d) {
 // Register budget of the face-flux kernel (blocks of 256 threads; no spills, ptxas sm_103a).
 template <int D, typename R> struct FluxKernelRegs { static constexpr int value = D == 2 ? 64 : 72; };
 template <int D> struct FluxKernelRegs<D, float> { static constexpr int value = 48; };
-template <int D> struct FluxKernelRegs<D, df64> { static constexpr int value = D == 2 ? 48 : 64; };
+template <int D> struct FluxKernelRegs<D, df64> { static constexpr int value = 64; };
 
 // grid: x over (element, face node) of one direction, y = direction d
 template <int D, int N, typename R>
