@@ -13,8 +13,8 @@ constexpr int kMaxCoefDelay = 16;
 // Operator tables in FP64; kernels convert entries to their arithmetic type.
 struct OpTables {
   double Q[3][kMaxN * kMaxN];  // (2/h_d) omega_a l_i'(xi_a) / omega_i, entry [i*N + a]
-  double Lp[3][kMaxN];         // (2/h_d) l_i(+1) / omega_i
-  double Lm[3][kMaxN];         // (2/h_d) l_i(-1) / omega_i
+  double Lp[3][kMaxN];         // (1/h_d) l_i(+1) / omega_i: half the lift (the stored
+  double Lm[3][kMaxN];         // (1/h_d) l_i(-1) / omega_i   face fluxes are doubled)
   double Tp[kMaxN];            // l_a(+1): trace at the high face
   double Tm[kMaxN];            // l_a(-1): trace at the low face
   double xi[kMaxN];            // Gauss nodes on [-1, 1]

@@ -147,7 +147,10 @@ void build_tables(adg_solver* s) {
         T.Q[d][i * N + a] = (double)q;
         T.Qf[d][i * N + a] = split2(q);
       }
-      long double vp = sc * lp[i] / (long double)wd[i], vm = sc * lm[i] / (long double)wd[i];
+      // lift coefficients (2/h) l_i(+-1) / omega_i, halved: the face-flux kernel stores
+      // twice the numerical flux
+      long double vp = 0.5L * sc * lp[i] / (long double)wd[i];
+      long double vm = 0.5L * sc * lm[i] / (long double)wd[i];
       T.Lp[d][i] = (double)vp;
       T.Lm[d][i] = (double)vm;
       T.Lpf[d][i] = split2(vp);

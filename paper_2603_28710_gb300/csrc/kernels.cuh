@@ -122,7 +122,11 @@ __device__ __forceinline__ void side_flux(const R (&w)[D + 2], int d, R gamma, R
   fd[D + 1] = (w[D + 1] + p) * ud;
 }
 
-// Rusanov flux along +e_d (Eq. 8) with lambda = 1/2 max(sqrt(|u|^2 + c^2)) (Eq. 9).
+// Twice the Rusanov flux along +e_d (Eq. 8) with lambda = 1/2 max(sqrt(|u|^2 + c^2))
+// (Eq. 9): f = F(w-) + F(w+) + lambda (w- - w+).  The factor 1/2 is folded into the lift
+// coefficients of the volume kernel (one operation less per value; scaling by two is
+// exact, so the results equal those of the halved form).  Stored fluxes, the ring of
+// subdomain-face levels and their AT combinations all carry the factor two.
 template <int D, typename R>
 __device__ __forceinline__ void llf_flux(const R (&wm)[D + 2], const R (&wp)[D + 2], int d,
                                          R gamma, R (&f)[D + 2]) {
@@ -146,9 +150,9 @@ __device__ __forceinline__ void llf_flux(const R (&wm)[D + 2], const R (&wp)[D +
     side_flux<D, R>(wm, d, gamma, gm1, fm, sm);
     side_flux<D, R>(wp, d, gamma, gm1, fp, sp);
   }
-  const R hl = scale_pow2(r_sqrt(r_max(sm, sp)), 0.25f);  // lambda / 2, lambda = sqrt(max) / 2
+  const R lam = scale_pow2(r_sqrt(r_max(sm, sp)), 0.5f);
 #pragma unroll
-  for (int v = 0; v < NV; ++v) f[v] = R(0.5f) * (fm[v] + fp[v]) + hl * (wm[v] - wp[v]);
+  for (int v = 0; v < NV; ++v) f[v] = r_fma(lam, wm[v] - wp[v], fm[v] + fp[v]);
 }
 
 // Transverse coordinates of face node j of a face normal to d -> base node index of the
