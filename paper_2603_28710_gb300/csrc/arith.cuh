@@ -118,10 +118,6 @@ __device__ __forceinline__ df64 sub_half(df64 w, df64 k) { return w - df64(0.5f 
 __device__ __forceinline__ double scale_pow2(double x, float p2) { return x * (double)p2; }
 __device__ __forceinline__ float scale_pow2(float x, float p2) { return x * p2; }
 
-// exact halving
-__device__ __forceinline__ double half(double x) { return 0.5 * x; }
-__device__ __forceinline__ float half(float x) { return 0.5f * x; }
-__device__ __forceinline__ df64 half(df64 x) { return df64(0.5f * x.hi, 0.5f * x.lo); }
 
 // accumulators: plain FMA chains for the native types
 __device__ __forceinline__ double acc_zero(double) { return 0.0; }

@@ -140,11 +140,6 @@ __device__ __forceinline__ df64acc acc_fma(df64 a, df64 b, df64acc t) {
   c = __fmaf_rn(a.lo, b.hi, c);
   return df64acc{s, c};
 }
-__device__ __forceinline__ df64acc acc_add(df64 a, df64acc t) {
-  float s, se;
-  two_sum(t.s, a.hi, s, se);
-  return df64acc{s, __fadd_rn(t.c, __fadd_rn(se, a.lo))};
-}
 __device__ __forceinline__ df64 acc_result(df64acc t) {
   float zh, zl;
   two_sum(t.s, t.c, zh, zl);

@@ -389,10 +389,6 @@ struct Update<double> {
   }
 };
 
-// One element tile (tile index `tile`) of the volume/update kernel.  A is read through a
-// reference so the batched kernels can pass per-instance arguments kept in device memory.
-// Shared memory of the volume kernel: the pointwise fluxes of the tile, then (kStage) the
-// per-thread staging slots of the RK operands (FP64 solution, FP32 stage register).
 // Pointwise fluxes of a tile in shared memory: [EPB][D][NV][ND] values of R, except for
 // the 2D FP32 pairs, which keep pairs of variables together for the packed sweeps:
 // [EPB][D][NV/2][ND] of float4 {hi_v, hi_v+1, lo_v, lo_v+1}.  (In 3D the odd variable
@@ -406,6 +402,9 @@ constexpr size_t vol_flux_bytes() {
                                    : sizeof(R) * T::EPB * D * T::NV * T::ND;
 }
 
+// Shared memory of the volume kernel: the pointwise fluxes of the tile, then (kStage) the
+// per-thread staging slots of the RK operands (FP64 solution; stage register in the
+// operator's storage type).  The trace epilogue reuses the flux area.
 template <int D, int N, typename R, int TT, bool kStage>
 struct VolSmem {
   using T = Tile<D, N, TT>;
@@ -431,13 +430,15 @@ __device__ __forceinline__ void cp_async_val(float2* smem, const float2* gmem) {
 __device__ __forceinline__ float from_stored(float v) { return v; }
 __device__ __forceinline__ df64 from_stored(float2 v) { return df64(v.x, v.y); }
 
+// One element tile (tile index `tile`) of the volume/update kernel.  A is read through a
+// reference so the batched kernels can pass per-instance arguments kept in device memory.
 template <int D, int N, typename R, int TT, bool kStage = false>
 __device__ __forceinline__ void vol_body(const VolArgs& A, int tile, unsigned char* smem_raw) {
   using T = Tile<D, N, TT>;
   using S = typename Arith<R>::S;
   using SM = VolSmem<D, N, R, TT, kStage>;
   constexpr int ND = T::ND, NF = T::NF, NV = T::NV, EPB = T::EPB;
-  R* sF = reinterpret_cast<R*>(smem_raw);  // [EPB][D][NV][ND]
+  R* sF = reinterpret_cast<R*>(smem_raw);  // [EPB][D][NV][ND] (packed sweeps: sF4 below)
   double* sW = reinterpret_cast<double*>(smem_raw + SM::W_OFF);  // [NV][THREADS] (kStage)
   S* sQ = reinterpret_cast<S*>(smem_raw + SM::Q_OFF);            // [NV][THREADS] (kStage)
   const int el = threadIdx.x / ND, node = threadIdx.x - el * ND;
