@@ -347,6 +347,55 @@ def tgv_run(adg, stream, k=3):
     return out
 
 
+def learned_run(adg, stream, k=2, err_steps=24):
+    """Learned ghost-trace predictor on its evaluation case (3D Taylor-Green vortex, 64^3
+    hexes, p = 3, 8x8x8 subdomains, L = 4, N_p = 2, CK4(5), CFL 0.1, FP64 operator) against
+    the plain AT extrapolation of the same stored traces: throughput (one benchmark step =
+    8 time steps) and the relative delay error after err_steps time steps against the
+    synchronous run (|w - w_sync| / |w_sync - w_0|)."""
+    import torch
+    from paper_2603_28710_gb300 import learned
+    if not os.path.exists(learned.MODEL_PATH):
+        return None
+    model, _ = learned.load()
+    kw = dict(dim=3, n_elem=(64, 64, 64), degree=3, lo=(0, 0, 0), hi=(2 * np.pi,) * 3,
+              P=(8, 8, 8), rk="ck45", cfl=0.1, precision="fp64", stream=stream.cuda_stream)
+    ndof = 5 * 64 ** 3 * 4 ** 3
+    ref = adg.Solver(flux="sync", **kw)
+    ref.init_tgv(0.1)
+    u0 = ref.get_state()
+    ref.step(err_steps)
+    u_sync = ref.get_state()
+    ref.close()
+    out = {}
+    for name, flux, trust in (("at_trace", "at_trace", None), ("learned", "learned", 1.0)):
+        s = adg.Solver(flux=flux, max_delay=4, at_np=2, **kw)
+        if trust is not None:
+            s.set_learned_model(model, trust)
+        s.init_tgv(0.1)
+        s.step(err_steps)
+        err = float(np.linalg.norm(s.get_state() - u_sync) / np.linalg.norm(u_sync - u0))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(8 * k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        s.close()
+        out[name] = {"value": ndof * 5 * 8 * k / (ms * 1e-3) / 1e9,
+                     "delay_error_vs_sync": err}
+    out["learned"]["trust"] = 1.0
+    out["speedup_vs_fp64_at"] = out["learned"]["value"] / out["at_trace"]["value"]
+    out["delay_error_ratio_vs_at"] = (out["learned"]["delay_error_vs_sync"]
+                                      / out["at_trace"]["delay_error_vs_sync"])
+    out["workload"] = ("3D Taylor-Green vortex 64^3 hexes p=3, 8x8x8 subdomains, CAA L=4, "
+                       "N_p=2, CK4(5), CFL 0.1, FP64 operator; delay error after "
+                       f"{err_steps} steps against the synchronous run")
+    out["unit"] = METRIC
+    return out
+
+
 # ---- GPU arm -----------------------------------------------------------------------------
 def run_gpu(args, rank, world, local_rank):
     import torch
@@ -476,6 +525,9 @@ def run_gpu(args, rank, world, local_rank):
     tgv = None
     if world == 1 and not args.no_3d:
         tgv = tgv_run(adg, stream)
+    learned_line = None
+    if world == 1 and not args.no_learned:
+        learned_line = learned_run(adg, stream)
 
     clocks = clk.summary()
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
@@ -491,7 +543,8 @@ def run_gpu(args, rank, world, local_rank):
             "kernels": {"vol_kernel": {"ms_per_launch": vol_ms / max(vol_n, 1), "launches": vol_n},
                         "flux_kernel": {"ms_per_launch": flux_ms / max(flux_n, 1),
                                         "launches": flux_n}},
-            "variants": variants, "batched": batched, "taylor_green_3d": tgv}
+            "variants": variants, "batched": batched, "taylor_green_3d": tgv,
+            "learned_ghost": learned_line}
     print(json.dumps(line), flush=True)
 
 
@@ -509,6 +562,8 @@ def main():
     ap.add_argument("--variant-steps", type=int, default=10)
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-instances run")
     ap.add_argument("--no-3d", action="store_true", help="skip the 3D Taylor-Green runs")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip the learned ghost-trace predictor run")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -1,7 +1,8 @@
 // Learned ghost-trace predictor: a small MLP, 4 inputs -> 64 -> 64 -> 1, tanh hidden
 // activations, BF16 weights read into FP32 and FP32 accumulation everywhere.  Kernels for
-// the mean-squared-error gradient of a sample set (forward + backward), an Adam step on
-// FP32 master weights that refreshes their BF16 copy, and inference.
+// the mean-squared-error gradient of a sample set (forward + backward, FP32 pipe), an Adam
+// step on FP32 master weights that refreshes their BF16 copy, and inference (the hidden
+// layer on the tensor cores).
 //
 // Parameter layout (kMlpParams = 4545 values):
 //   W1[64][4] | b1[64] | W2[64][64] | b2[64] | w3[64] | b3
@@ -130,14 +131,128 @@ mlp_grad_kernel(const uint16_t* __restrict__ pbf, const float* __restrict__ x,
   if (tid == 0) atomicAdd(loss, red[0]);
 }
 
-__global__ void mlp_forward_kernel(const uint16_t* __restrict__ pbf, const float* __restrict__ x,
-                                   int n, float* __restrict__ y) {
-  __shared__ float W[4548];
-  for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x) W[i] = bf16_to_float(pbf[i]);
+// ---- inference on the tensor cores --------------------------------------------------
+// The 64 x 64 hidden layer of a tile of 16 samples is a [16 x 64] x [64 x 64] product: warp-
+// level BF16 MMAs (mma.sync m16n8k16, FP32 accumulation).  The BF16 weights enter exactly;
+// the FP32 activations of the first layer are split into three BF16 terms
+// h = h0 + h1 + h2 (each the BF16 rounding of what the previous terms leave; residual below
+// 2^-24 |h|), so the product keeps FP32 accuracy at three MMAs per k-step.  The 4 -> 64
+// input layer, the tanh activations and the 64 -> 1 output layer stay on the FP32 pipe.
+//
+// Fragment layouts of mma.m16n8k16 (PTX ISA; g = lane / 4, t = lane % 4):
+//   A (16 x 16, row-major, 4 x b32 = 8 bf16): reg 0 = rows g, cols 2t, 2t+1; reg 1 = row g+8;
+//     reg 2 = row g, cols 2t+8, 2t+9; reg 3 = row g+8, cols 2t+8, 2t+9 (lower half first)
+//   B (16 x 8, column-major, 2 x b32): reg 0 = rows (k) 2t, 2t+1 of column (n) g; reg 1 =
+//     rows 2t+8, 2t+9
+//   C/D (16 x 8, f32): c0, c1 = row g, cols 2t, 2t+1; c2, c3 = row g+8
+
+__device__ __forceinline__ unsigned short bf16_bits_rn(float f) { return float_to_bf16(f); }
+
+__device__ __forceinline__ unsigned pack_bf16(float lo_col, float hi_col) {
+  return (unsigned)bf16_bits_rn(lo_col) | ((unsigned)bf16_bits_rn(hi_col) << 16);
+}
+
+// three-term BF16 split of two adjacent activations into three packed registers
+__device__ __forceinline__ void split3(float a, float b, unsigned& r0, unsigned& r1, unsigned& r2) {
+  const float a0 = bf16_to_float(bf16_bits_rn(a)), b0 = bf16_to_float(bf16_bits_rn(b));
+  const float a1r = a - a0, b1r = b - b0;  // exact (Sterbenz)
+  const float a1 = bf16_to_float(bf16_bits_rn(a1r)), b1 = bf16_to_float(bf16_bits_rn(b1r));
+  r0 = pack_bf16(a0, b0);
+  r1 = pack_bf16(a1, b1);
+  r2 = pack_bf16(a1r - a1, b1r - b1);
+}
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const unsigned (&a)[4], unsigned b0,
+                                         unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+      "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+constexpr int kInferWarps = 4;
+
+__global__ void __launch_bounds__(32 * kInferWarps)
+mlp_forward_mma_kernel(const uint16_t* __restrict__ pbf, const float* __restrict__ x, int n,
+                       float* __restrict__ y) {
+  __shared__ float Wf[kW2];                  // W1 | b1 (FP32)
+  __shared__ float Wo[kMlpParams - kB2];     // b2 | w3 | b3 (FP32)
+  __shared__ __align__(16) uint16_t W2[64 * 64];  // [n = out][k = in], BF16
+  for (int i = threadIdx.x; i < kW2; i += blockDim.x) Wf[i] = bf16_to_float(pbf[i]);
+  for (int i = threadIdx.x; i < kMlpParams - kB2; i += blockDim.x) Wo[i] = bf16_to_float(pbf[kB2 + i]);
+  for (int i = threadIdx.x; i < 64 * 64; i += blockDim.x) W2[i] = pbf[kW2 + i];
   __syncthreads();
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-    float xi[4] = {x[(size_t)s * 4], x[(size_t)s * 4 + 1], x[(size_t)s * 4 + 2], x[(size_t)s * 4 + 3]};
-    y[s] = mlp_eval(W, xi);
+  const unsigned* W2w = reinterpret_cast<const unsigned*>(W2);  // pairs along k
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int tiles = (n + 15) / 16;
+  for (int tile = blockIdx.x * kInferWarps + (threadIdx.x >> 5); tile < tiles;
+       tile += gridDim.x * kInferWarps) {
+    const int r0 = tile * 16 + g, r1 = r0 + 8;
+    float x0[4], x1[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      x0[i] = r0 < n ? x[(size_t)r0 * 4 + i] : 0.0f;
+      x1[i] = r1 < n ? x[(size_t)r1 * 4 + i] : 0.0f;
+    }
+    float acc[8][4];
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[j][q] = 0.0f;
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+      // first-layer activations of this k-block: columns c0, c0+1 and c0+8, c0+9 of rows r0, r1
+      const int c0 = kk * 16 + 2 * t;
+      float h[2][4];  // [row][col c0, c0+1, c0+8, c0+9]
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int c = c0 + (q & 1) + (q >> 1) * 8;
+        float z0 = Wf[kB1 + c], z1 = Wf[kB1 + c];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          z0 = fmaf(Wf[kW1 + c * 4 + i], x0[i], z0);
+          z1 = fmaf(Wf[kW1 + c * 4 + i], x1[i], z1);
+        }
+        h[0][q] = tanhf(z0);
+        h[1][q] = tanhf(z1);
+      }
+      unsigned a[3][4];
+      split3(h[0][0], h[0][1], a[0][0], a[1][0], a[2][0]);
+      split3(h[1][0], h[1][1], a[0][1], a[1][1], a[2][1]);
+      split3(h[0][2], h[0][3], a[0][2], a[1][2], a[2][2]);
+      split3(h[1][2], h[1][3], a[0][3], a[1][3], a[2][3]);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int nrow = j * 8 + g;  // output unit of this lane's B column
+        const unsigned b0 = W2w[(nrow * 64 + kk * 16 + 2 * t) >> 1];
+        const unsigned b1 = W2w[(nrow * 64 + kk * 16 + 2 * t + 8) >> 1];
+        mma_bf16(acc[j], a[0], b0, b1);
+        mma_bf16(acc[j], a[1], b0, b1);
+        mma_bf16(acc[j], a[2], b0, b1);
+      }
+    }
+    // second activation and the output layer: this lane holds columns 2t, 2t+1 of each
+    // 8-column block for rows r0 (acc[j][0..1]) and r1 (acc[j][2..3])
+    float y0 = 0.0f, y1 = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int c = j * 8 + 2 * t + q;
+        const float w3 = Wo[kW3 - kB2 + c], b2 = Wo[c];
+        y0 = fmaf(w3, tanhf(acc[j][q] + b2), y0);
+        y1 = fmaf(w3, tanhf(acc[j][2 + q] + b2), y1);
+      }
+    y0 += __shfl_xor_sync(0xffffffffu, y0, 1);
+    y0 += __shfl_xor_sync(0xffffffffu, y0, 2);
+    y1 += __shfl_xor_sync(0xffffffffu, y1, 1);
+    y1 += __shfl_xor_sync(0xffffffffu, y1, 2);
+    if (t == 0) {
+      const float b3 = Wo[kB3 - kB2];
+      if (r0 < n) y[r0] = y0 + b3;
+      if (r1 < n) y[r1] = y1 + b3;
+    }
   }
 }
 
@@ -169,8 +284,10 @@ __global__ void to_bf16_kernel(const float* __restrict__ p, uint16_t* __restrict
 
 cudaError_t mlp_infer(const uint16_t* params, const float* x, int64_t n, float* y, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  const int blocks = (int)((n + 255) / 256) < 152 * 8 ? (int)((n + 255) / 256) : 152 * 8;
-  mlp_forward_kernel<<<blocks, 256, 0, s>>>(params, x, (int)n, y);
+  const int64_t tiles = (n + 15) / 16;
+  const int64_t want = (tiles + kInferWarps - 1) / kInferWarps;
+  const int blocks = (int)(want < 152 * 16 ? want : 152 * 16);
+  mlp_forward_mma_kernel<<<blocks, 32 * kInferWarps, 0, s>>>(params, x, (int)n, y);
   return cudaGetLastError();
 }
 
@@ -213,9 +330,7 @@ adg_status adg_mlp_forward(const uint16_t* params_bf16, const float* x, int64_t 
   if (!params_bf16 || !x || !y || n < 0) return mfail(ADG_ERR_INVALID, "bad arguments");
   if (n == 0) return ADG_OK;
   if (n >= ((int64_t)1 << 31)) return mfail(ADG_ERR_INVALID, "too many samples");
-  const int blocks = (int)((n + 255) / 256) < 152 * 8 ? (int)((n + 255) / 256) : 152 * 8;
-  mlp_forward_kernel<<<blocks, 256, 0, (cudaStream_t)cuda_stream>>>(params_bf16, x, (int)n, y);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = mlp_infer(params_bf16, x, n, y, (cudaStream_t)cuda_stream);
   return e == cudaSuccess ? ADG_OK : mfail(ADG_ERR_CUDA, cudaGetErrorString(e));
 }
 

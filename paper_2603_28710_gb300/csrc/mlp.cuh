@@ -1,5 +1,5 @@
 // Shared pieces of the learned ghost-trace predictor (mlp.cu and the solver's learned
-// flux correction): parameter layout, BF16 conversions and single-sample inference.
+// flux correction): parameter layout and BF16 conversions.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -24,25 +24,5 @@ __host__ __device__ __forceinline__ uint16_t float_to_bf16(float f) {
   return (uint16_t)(u >> 16);
 }
 
-// y = w3 . tanh(W2 tanh(W1 x + b1) + b2) + b3 with W (FP32 copy of the BF16 weights) in
-// shared memory; FP32 accumulation.
-__device__ __forceinline__ float mlp_eval(const float* W, const float* x) {
-  float h1[64];
-#pragma unroll
-  for (int j = 0; j < 64; ++j) {
-    float z = W[kB1 + j];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) z = fmaf(W[kW1 + j * 4 + i], x[i], z);
-    h1[j] = tanhf(z);
-  }
-  float y = W[kB3];
-  for (int j = 0; j < 64; ++j) {
-    float z = W[kB2 + j];
-#pragma unroll
-    for (int i = 0; i < 64; ++i) z = fmaf(W[kW2 + j * 64 + i], h1[i], z);
-    y = fmaf(W[kW3 + j], tanhf(z), y);
-  }
-  return y;
-}
 
 }  // namespace adg
