@@ -6,10 +6,21 @@ L = 3 and the AT flux (N_p + 1 = 5 stored levels), CK4(5) low-storage RK, CFL 0.
 One benchmark step is one full schedule cycle: L + N_p + 1 = 8 time steps (5 communication
 steps, 3 delayed ones), i.e. 40 RK stages over 6,553,600 DoF.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--precision fp64]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--precision fp64|df64|fp32] [--no-cpu-baseline] [--no-variants]
+                  [--no-batch] [--no-3d] [--no-learned]
 
 Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank runs an independent
 replica on its own GPU ("replicas only": the path has no exchange between GPUs).
+Besides the headline (value, e2e through the C ABI with pinned host buffers, roofline of
+the volume kernel from live CUDA events, clocks sampled by nvidia-smi, the oracle's CPU
+throughput, launch count) the line carries:
+  variants         the same workload with the FP64, FP32-pair and FP32 operators, with
+                   their L2 errors against the exact vortex;
+  batched          64 uneven vortex instances in one CUDA graph per step vs separate handles;
+  taylor_green_3d  the 3D Taylor-Green vortex (64^3, p = 3) in each operator arithmetic;
+  learned_ghost    the learned ghost-trace predictor against plain AT on its 3D case.
+`--impl reference` times the CPU oracle on the same workload instead (rank 0 only).
 """
 from __future__ import annotations
 
