@@ -283,10 +283,13 @@ void adg_batch_destroy(adg_batch* b);
  * All pointers below are DEVICE pointers; work is enqueued on cuda_stream. */
 int adg_mlp_num_params(void);
 /* Mean squared error over n samples (x[n][4], target[n]): ADDS d(loss)/d(params) to grad
- * (FP32, one value per parameter) and the loss to *loss (one float). */
+ * (FP32, one value per parameter) and the loss to *loss (one float).  Forward and backward
+ * pass in FP32 arithmetic with the BF16 weights. */
 adg_status adg_mlp_grad(const uint16_t* params_bf16, const float* x, const float* target,
                         int64_t n, float* grad, float* loss, void* cuda_stream);
-/* y[n] = MLP(x[n][4]). */
+/* y[n] = MLP(x[n][4]).  The hidden 64 x 64 layer runs on the tensor cores (BF16 MMA with
+ * FP32 accumulation; the FP32 activations enter as three BF16 terms, so the result has
+ * FP32 accuracy); the solver's learned flux uses the same kernel. */
 adg_status adg_mlp_forward(const uint16_t* params_bf16, const float* x, int64_t n, float* y,
                            void* cuda_stream);
 /* One Adam step (step counter t >= 1) on FP32 master params with moments m, v; writes the
