@@ -204,27 +204,39 @@ def oracle_sample(time_steps):
 
 
 def run_reference(args, rank, world):
-    """The oracle as the reference arm: one RK time step of the full workload per step,
-    single-threaded, on the host cores (rank 0 only)."""
+    """The oracle as the reference arm, single-threaded on the host cores (rank 0 only).
+    Each step is a bounded sample of the workload: one RK time step (5 stages), or one
+    stage (one operator evaluation) when K time steps would take more than about two
+    minutes."""
     if rank != 0:
         return
     o = make_oracle()
     o.step(args.warmup)
-    per = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        o.step(1)
-        per.append(time.perf_counter() - t0)
-    total = sum(per)
     ndof = 4 * N_ELEM * N_ELEM * (DEGREE + 1) ** 2
-    value = ndof * 5 * args.steps / total / 1e9
+    t0 = time.perf_counter()
+    o.step(1)
+    t_step = time.perf_counter() - t0
+    per_stage = args.steps * t_step > 120.0
+    total, stages = (0.0, 0) if per_stage else (t_step, 5)
+    u = o.get_state() if per_stage else None
+    for _ in range(args.steps if per_stage else args.steps - 1):
+        t0 = time.perf_counter()
+        if per_stage:
+            o.rhs(u)
+            stages += 1
+        else:
+            o.step(1)
+            stages += 5
+        total += time.perf_counter() - t0
+    value = ndof * stages / total / 1e9
+    sample = ("one RK stage (operator evaluation)" if per_stage else "one RK time step (5 stages)")
     line = {"metric": METRIC, "value": value, "unit": METRIC, "impl": "reference", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config("fp64"),
             "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
-                             "sample": "one RK time step (5 stages) of the full 256^2 p=4 "
-                                       "workload per step, single-threaded C oracle"},
+                             "sample": f"{sample} of the full 256^2 p=4 workload per step, "
+                                       "single-threaded C oracle"},
             "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
