@@ -3,7 +3,7 @@
 Every arithmetic step runs in the library's CUDA kernels (trace logging, sample
 construction, MLP forward/backward, Adam); torch only holds device buffers.
 
-Recipe (the committed model ``models/ghost_mlp.npz``); network inputs per scalar channel:
+Recipe (the committed model ``trained/ghost_mlp.npz``); network inputs per scalar channel:
 the two level differences in units of the level spread, the integer delay k / 8 and the RK
 stage offset c_m; target: (truth - AT extrapolation) / (AT minus linear extrapolation), a
 learned next-order step, kept where |target| <= 2:
@@ -26,7 +26,7 @@ from . import adg
 from .inputs import vortex_params
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-MODEL_PATH = os.path.join(HERE, "models", "ghost_mlp.npz")
+MODEL_PATH = os.path.join(HERE, "trained", "ghost_mlp.npz")
 N_PARAMS = 4545
 
 
