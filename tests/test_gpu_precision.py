@@ -158,3 +158,19 @@ def test_fp32_rhs_random_state(dim, n_elem, p):
     inc = np.linalg.norm((kg - ko) * dt) / np.linalg.norm(u)
     print(f"fp32 rhs {dim}D p={p}: increment error {inc:.2e}")
     assert inc < 1e-7
+
+
+def test_fp32_3d_steps():
+    kw = dict(P=(2, 2, 2), max_delay=2, flux="at", rk="ck45", dt=0.01)
+    dim, n_elem, p = 3, (4, 4, 4), 2
+    lo, hi = (0.0,) * 3, (2 * np.pi,) * 3
+    s = adg.Solver(dim=dim, n_elem=n_elem, degree=p, lo=lo, hi=hi, precision="fp32", **kw)
+    o = O.Oracle(dim=dim, n_elem=n_elem, degree=p, lo=lo, hi=hi, **kw)
+    u0 = o.init_tgv(0.3)
+    s.set_state(u0)
+    o.set_state(u0)
+    s.step(6)
+    o.step(6)
+    e6 = rel(s.get_state(), o.get_state())
+    print(f"fp32 3D Taylor-Green 4^3 p=2, 6 AT steps: relative L2 error {e6:.2e}")
+    assert e6 < 1e-6
