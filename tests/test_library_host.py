@@ -98,3 +98,43 @@ def test_bad_arguments_rejected_without_gpu():
         adg.host_gauss(0)
     with pytest.raises(adg.AdgError):
         adg.host_at_coeffs(9, 1.0)
+
+
+@pytest.mark.parametrize("kw,msg", [
+    (dict(dim=2, n_elem=(6, 6), P=(4, 4), flux="at", max_delay=2), "divide"),
+    (dict(dim=2, n_elem=(8, 8), degree=0), "degree"),
+    (dict(dim=2, n_elem=(8, 8), degree=8), "degree"),
+    (dict(dim=3, n_elem=(2, 2, 2), degree=6), "3D"),
+    (dict(dim=2, n_elem=(8, 8), flux="std", max_delay=0, P=(2, 2)), "max_delay"),
+    (dict(dim=2, n_elem=(8, 8), flux="learned", max_delay=2, P=(2, 2), at_np=3), "at_np"),
+    (dict(dim=2, n_elem=(8, 8), delay_mode="random", random_delay_max=16, flux="at",
+          P=(2, 2), max_delay=2), "random_delay_max"),
+    (dict(dim=2, n_elem=(8, 8), gamma=1.0), "gamma"),
+    (dict(dim=2, n_elem=(8, 8), cfl=0.0, dt=0.0), "dt"),
+])
+def test_create_rejects_bad_configurations_without_gpu(kw, msg):
+    # validation happens before any device work: status and message, no CUDA call
+    with pytest.raises(adg.AdgError, match=msg) as e:
+        adg.Solver(**kw)
+    assert e.value.status in (1, 2)
+
+
+def test_empty_and_null_inputs_without_gpu():
+    import ctypes
+    L = adg.lib()
+    # an empty sample set is a no-op; missing buffers are refused
+    assert L.adg_mlp_forward(None, None, 0, None, None) == 1  # NULL params: invalid
+    p = (ctypes.c_uint16 * adg.lib().adg_mlp_num_params())()
+    x = (ctypes.c_float * 4)()
+    y = (ctypes.c_float * 1)()
+    assert L.adg_mlp_forward(p, x, 0, y, None) == 0
+    assert L.adg_mlp_grad(p, x, x, -1, y, y, None) == 1
+    # batches need at least one instance; NULL handles are refused, destroy is NULL-safe
+    h = ctypes.c_void_p()
+    assert L.adg_batch_create(0, None, None, None, None, 2, None, ctypes.byref(h)) == 1
+    assert L.adg_step(None, 1) == 1
+    n = ctypes.c_int64()
+    assert L.adg_checkpoint_bytes(None, ctypes.byref(n)) == 1
+    assert L.adg_checkpoint_restore(None, None, 0) == 1
+    L.adg_destroy(None)
+    L.adg_batch_destroy(None)
