@@ -337,18 +337,22 @@ def batched_run(adg, stream, k=6):
             "autotune_s": tune_s}
 
 
-def tgv_run(adg, stream, k=3):
+def tgv_run(adg, stream, k=3, total_steps=100):
     """3D Taylor-Green vortex, 64^3 hexes, p = 3, 8x8x8 subdomains, L = 4, AT flux,
     CK4(5), CFL 0.1: throughput per operator arithmetic (one benchmark step = one schedule
-    cycle of L + N_p + 1 = 8 time steps)."""
+    cycle of L + N_p + 1 = 8 time steps), and after total_steps RK steps from the initial
+    condition each form's relative L2 difference from the FP64 form and its drift of the
+    conserved totals (mass, momentum, energy; max over variables, relative)."""
     import torch
     out = {}
     ndof = 5 * 64 ** 3 * 4 ** 3
+    u64 = None
     for prec in ("fp64", "df64", "fp32"):
         s = adg.Solver(dim=3, n_elem=(64, 64, 64), degree=3, lo=(0, 0, 0), hi=(2 * np.pi,) * 3,
                        P=(8, 8, 8), max_delay=4, flux="at", rk="ck45", cfl=0.1, precision=prec,
                        stream=stream.cuda_stream)
         s.init_tgv(0.1)
+        c0 = s.conservation()
         s.step(8)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -360,10 +364,22 @@ def tgv_run(adg, stream, k=3):
         s.set_profiling(True)
         s.step(8)
         prof = s.get_profile()
+        s.set_profiling(False)
+        s.step(total_steps - 8 * (k + 2))
+        u = s.get_state()
+        c1 = s.conservation()
         s.close()
         out[prec] = {"value": ndof * 5 * 8 * k / (ms * 1e-3) / 1e9,
                      "vol_ms_per_launch": prof["vol"][0] / max(prof["vol"][1], 1),
-                     "flux_ms_per_launch": prof["flux"][0] / max(prof["flux"][1], 1)}
+                     "flux_ms_per_launch": prof["flux"][0] / max(prof["flux"][1], 1),
+                     f"conservation_drift_after_{total_steps}_steps":
+                         float(np.max(np.abs(c1 - c0)) / np.max(np.abs(c0)))}
+        if prec == "fp64":
+            u64 = u
+        else:
+            out[prec][f"rel_l2_diff_vs_fp64_after_{total_steps}_steps"] = float(
+                np.linalg.norm(u - u64) / np.linalg.norm(u64))
+        del u
     out["workload"] = ("3D Taylor-Green vortex 64^3 hexes p=3 (83.9M DoF), 8x8x8 subdomains, "
                        "CAA L=4, AT flux, CK4(5), CFL 0.1")
     out["unit"] = METRIC
