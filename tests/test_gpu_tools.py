@@ -1,0 +1,24 @@
+"""The package's command-line helpers on the GPU: the profiler driver runs a small case of
+each operator form in 2D and 3D and leaves a finite state."""
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2603_28710_gb300 import build
+    build.build()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "df64", "fp32"])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_profile_case_runs(dim, precision, capsys):
+    from paper_2603_28710_gb300 import profile_case
+    profile_case.main(["--dim", str(dim), "--n", "8", "--degree", "2", "--P", "2", "--L", "2",
+                       "--steps", "3", "--precision", precision])
+    out = capsys.readouterr().out
+    assert "finite=True" in out and f"dim={dim}" in out
