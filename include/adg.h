@@ -196,7 +196,10 @@ adg_status adg_checkpoint_restore(adg_solver* s, const void* buf, int64_t bytes)
 /* Kernel timing.  While enabled, adg_step records a CUDA event pair on the handle's stream
  * around every kernel it launches.  adg_get_profile waits for the stream and returns, per
  * kernel kind (0: face-flux kernel, 1: volume/update kernel), the summed device time in ms
- * and the launch count since profiling was enabled or last read; it then resets them. */
+ * and the launch count since profiling was enabled or last read; it then resets them.
+ * At most 2048 events are kept: when they are used up, adg_step waits for the stream once
+ * and folds the recorded pairs into the running totals (profiling is a diagnostic mode;
+ * with it off, adg_step never waits). */
 adg_status adg_set_profiling(adg_solver* s, int enable);
 adg_status adg_get_profile(adg_solver* s, double* ms, int64_t* launches);
 
@@ -225,12 +228,28 @@ adg_status adg_get_profile(adg_solver* s, double* ms, int64_t* launches);
  *                 layout as for adg_set_state; u is read, k written;
  *   count:        must equal n_dof;
  *   cuda_stream:  cudaStream_t the work is ordered on (NULL = legacy default stream).
- * The call enqueues the work and returns without waiting.  A mesh whose scratch
+ * The call enqueues the work and returns without waiting: the operator tables travel as
+ * a kernel argument and a kernel stores them into the scratch array, so no host memory is
+ * read after the call returns and no copy from pageable memory stalls the host.  A mesh
+ * whose scratch
  * (2 d + d) (d+2) n_elements (degree+1)^(d-1) doubles plus the tables exceeds
  * ADG_NOALLOC_SCRATCH_BYTES is rejected with ADG_ERR_INVALID; adg_last_error(NULL) says
  * how many bytes it needed.  Other errors: ADG_ERR_INVALID (arguments), ADG_ERR_CUDA. */
 adg_status adg_rhs_noalloc(const adg_mesh* mesh, int degree, double gamma, const double* u,
                            double* k, int64_t count, void* cuda_stream);
+
+/* Arithmetic peak probe (no counterpart in the paper; it supplies the denominators of the
+ * roofline fractions the library reports).  Measures, on the current device, the rate of
+ * one instruction kind with every warp slot busy on independent dependency chains:
+ *   kind 0: FP64 FMA; 1: FP32 FMA; 2: FP64 tensor MMA (mma.sync m8n8k4 f64);
+ *   3: FP64 FMA and FP64 MMA in alternate warps (shows whether the two paths add up);
+ *   4: packed FP32x2 FMA.
+ * tflops receives the best of three timed launches (about 50 ms each at the nominal
+ * rates) in TFLOP/s (an FMA counts as 2 flops, an m8n8k4 MMA as 512 per warp); ms
+ * (nullable) that launch's duration.  Allocates and frees a small device buffer and a
+ * private stream; waits for its own launches.  Errors: ADG_ERR_INVALID, ADG_ERR_CUDA
+ * (adg_last_error(NULL) has the text). */
+adg_status adg_measure_peak(int kind, double* tflops, double* ms);
 
 /* Message for the last failing call on s (NULL: on this thread, for calls without a
  * handle).  Valid until the next call on the same handle/thread. */

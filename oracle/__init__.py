@@ -11,8 +11,13 @@ flux with the paper's dissipation parameter (Eq. 8-9), the two-register LSERK up
 Parity status per function (what pins it lives in ``tests/test_oracle_*.py``):
   gauss, lagrange(+deriv), at_coeffs, rk_tableau, euler_flux, llf, schedule, rhs,
   step (SYNC / STD / AT / AT_TRACE), conservation, init_vortex, l2_error_vortex: pinned.
-  init_tgv: parity unpinned (the Taylor-Green initial condition is not in the paper; only
-  its invariants are checked).
+  init_tgv, dt_from_cfl: pinned by closed forms (test_oracle_init_dt.py): the Taylor-Green
+  initial condition (not in the paper) by its uniform temperature, zero z velocity, domain
+  means and pressure variance worked by hand, and its divergence-free velocity; the CFL
+  time step by hand-computed uniform states, the node maximum and the t_end rounding.
+
+The all-cores timing variant (``Oracle(parallel=True)``) is the same C source compiled with
+OpenMP over elements; its results equal the single-threaded build's.
 """
 from __future__ import annotations
 
@@ -27,25 +32,30 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "adgref.c")
 _HDR = os.path.join(_HERE, "adgref.h")
 _LIB_PATH = os.path.join(_HERE, "_build", "libadgref.so")
+# all-cores variant: the same source with OpenMP over elements (timing only; same results)
+_LIB_PATH_OMP = os.path.join(_HERE, "_build", "libadgref_omp.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {}
 
 FLUX = {"sync": 0, "std": 1, "at": 2, "at_trace": 3}
 DELAY = {"caa": 0, "random": 1}
 RK = {"rk22": 0, "rk33": 1, "ck45": 2}
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (-O2, no FMA contraction, no fast-math)."""
-    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
-    stale = (not os.path.exists(_LIB_PATH)) or any(
-        os.path.getmtime(p) > os.path.getmtime(_LIB_PATH) for p in (_SRC, _HDR))
+def build(force: bool = False, parallel: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, no FMA contraction, no fast-math); parallel=True
+    builds the OpenMP variant used for the all-cores timing."""
+    path = _LIB_PATH_OMP if parallel else _LIB_PATH
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    stale = (not os.path.exists(path)) or any(
+        os.path.getmtime(p) > os.path.getmtime(path) for p in (_SRC, _HDR))
     if force or stale:
-        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+        tmp = path + f".{os.getpid()}.tmp"
+        extra = ["-fopenmp"] if parallel else []
         subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-                               "-shared", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+                               *extra, "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, path)
+    return path
 
 
 class _Params(ctypes.Structure):
@@ -58,11 +68,10 @@ class _Params(ctypes.Structure):
                 ("gamma", ctypes.c_double), ("dt", ctypes.c_double)]
 
 
-def lib():
-    global _lib
+def lib(parallel: bool = False):
     with _lock:
-        if _lib is None:
-            L = ctypes.CDLL(build())
+        if parallel not in _libs:
+            L = ctypes.CDLL(build(parallel=parallel))
             D, I, I64, U64 = ctypes.c_double, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64
             P = ctypes.c_void_p
             L.adgref_gauss.argtypes = [I, P, P]
@@ -95,8 +104,15 @@ def lib():
             L.adgref_dt_from_cfl.argtypes = [P, P, D, D]
             L.adgref_dt_from_cfl.restype = D
             L.adgref_info.argtypes = [P, P, P, P]
-            _lib = L
-    return _lib
+            L.adgref_threads.argtypes = []
+            L.adgref_threads.restype = I
+            _libs[parallel] = L
+    return _libs[parallel]
+
+
+def threads(parallel: bool = False) -> int:
+    """Threads the oracle's element loops use (1 unless parallel)."""
+    return int(lib(parallel).adgref_threads())
 
 
 def _ptr(a: np.ndarray):
@@ -180,7 +196,7 @@ class Oracle:
 
     def __init__(self, dim=2, n_elem=(16, 16), lo=(-5.0, -5.0), hi=(5.0, 5.0), degree=2,
                  P=(1, 1), max_delay=1, flux="sync", rk="ck45", delay_mode="caa",
-                 random_delay_max=0, at_np=0, seed=0, gamma=1.4, dt=1e-3):
+                 random_delay_max=0, at_np=0, seed=0, gamma=1.4, dt=1e-3, parallel=False):
         pr = _Params()
         pr.dim = dim
         P = tuple(P) + (1,) * (3 - len(P))
@@ -199,7 +215,7 @@ class Oracle:
         pr.seed = seed & 0xFFFFFFFFFFFFFFFF
         pr.gamma = gamma
         pr.dt = dt
-        self._L = lib()
+        self._L = lib(parallel)
         self._h = self._L.adgref_create(ctypes.byref(pr))
         if not self._h:
             raise ValueError("oracle rejected the parameters")

@@ -19,6 +19,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define MAXN 9   /* up to degree 8 */
 
@@ -568,7 +571,7 @@ adgref* adgref_create(const adgref_params* prm) {
   int64_t bsz = o->nslot * o->depth * nf * o->nv;
   o->buf = calloc(bsz + 1, sizeof(double));
   o->bufp = calloc(prm->flux == ADGREF_FLUX_AT_TRACE ? bsz + 1 : 1, sizeof(double));
-  o->F = malloc(sizeof(double) * 3 * o->nv * nd);
+  o->F = malloc(sizeof(double) * 3 * o->nv * nd);  /* scratch of the one-element calls */
   o->V = malloc(sizeof(double) * o->nv * nd);
   o->S = malloc(sizeof(double) * o->nv * nd);
   return o;
@@ -677,10 +680,11 @@ static void face_flux(adgref* o, int64_t e, int f, int fq, const double* wm, con
 /* Element residual k_e = M^{-1} [ (grad phi_i, F(w_h)) - <phi_i, n . F^> ]  (Eq. 6-7),   */
 /* by dense quadrature over all basis-function / quadrature-point pairs.                   */
 /* ------------------------------------------------------------------------------------ */
-static void element_rhs(adgref* o, const double* u, int64_t e, int stage, int mode, double* out) {
+/* F, V, S: scratch of 3 nv nd, nv nd and nv nd values (one set per thread). */
+static void element_rhs(adgref* o, const double* u, int64_t e, int stage, int mode, double* out,
+                        double* F, double* V, double* S) {
   int nd = o->nd, nv = o->nv, dim = o->dim, nf = o->nf;
   int64_t ne = o->ne;
-  double* F = o->F;
   for (int q = 0; q < nd; ++q) {
     double wv[5], fv[5];
     for (int v = 0; v < nv; ++v) wv[v] = u[(v * ne + e) * nd + q];
@@ -695,8 +699,8 @@ static void element_rhs(adgref* o, const double* u, int64_t e, int stage, int mo
       for (int q = 0; q < nd; ++q)
         for (int d = 0; d < dim; ++d)
           s += o->wq[q] * o->grad_vol[(i * nd + q) * 3 + d] * F[(d * nv + v) * nd + q];
-      o->V[v * nd + i] = s;
-      o->S[v * nd + i] = 0.0;
+      V[v * nd + i] = s;
+      S[v * nd + i] = 0.0;
     }
   for (int f = 0; f < o->nfaces; ++f) {
     int dir = f / 2, side = f % 2;
@@ -718,19 +722,42 @@ static void element_rhs(adgref* o, const double* u, int64_t e, int stage, int mo
       face_flux(o, e, f, fq, wm, wp, normal, stage, mode, fh);
       for (int v = 0; v < nv; ++v)
         for (int i = 0; i < nd; ++i)
-          o->S[v * nd + i] += o->wfq[f * nf + fq] * o->phi_face[(f * nd + i) * nf + fq] * fh[v];
+          S[v * nd + i] += o->wfq[f * nf + fq] * o->phi_face[(f * nd + i) * nf + fq] * fh[v];
     }
   }
   for (int v = 0; v < nv; ++v) {
     double b[MAXN * MAXN * MAXN];
-    for (int i = 0; i < nd; ++i) b[i] = o->V[v * nd + i] - o->S[v * nd + i];
+    for (int i = 0; i < nd; ++i) b[i] = V[v * nd + i] - S[v * nd + i];
     lu_solve(nd, o->mlu, o->piv, b);
     for (int i = 0; i < nd; ++i) out[(v * ne + e) * nd + i] = b[i];
   }
 }
 
-void adgref_rhs(adgref* o, const double* u, double* k) {
-  for (int64_t e = 0; e < o->ne; ++e) element_rhs(o, u, e, 0, 0, k);
+/* Residual of every element.  Elements are independent (each writes its own output and,
+ * on storing steps, its own flux-buffer slots), so a build with OpenMP (-fopenmp, the
+ * all-cores timing variant) splits them over threads, each with its own scratch; the
+ * arithmetic of each element is the same in both builds, and so are the results. */
+static void all_elements_rhs(adgref* o, const double* u, int stage, int mode, double* out) {
+  size_t nsc = (size_t)o->nv * o->nd;
+#pragma omp parallel
+  {
+    double* F = malloc(sizeof(double) * 5 * nsc);
+    double* V = F + 3 * nsc;
+    double* S = V + nsc;
+#pragma omp for schedule(static)
+    for (int64_t e = 0; e < o->ne; ++e) element_rhs(o, u, e, stage, mode, out, F, V, S);
+    free(F);
+  }
+}
+
+void adgref_rhs(adgref* o, const double* u, double* k) { all_elements_rhs(o, u, 0, 0, k); }
+
+int adgref_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
 }
 
 void adgref_rhs_elements(adgref* o, const double* u, const int64_t* elems, int64_t n_sel,
@@ -741,7 +768,7 @@ void adgref_rhs_elements(adgref* o, const double* u, const int64_t* elems, int64
   (void)sz;
   for (int64_t s = 0; s < n_sel; ++s) {
     int64_t e = elems[s];
-    element_rhs(o, u, e, 0, 0, tmp);
+    element_rhs(o, u, e, 0, 0, tmp, o->F, o->V, o->S);
     for (int v = 0; v < o->nv; ++v)
       for (int i = 0; i < o->nd; ++i)
         k[(s * o->nv + v) * o->nd + i] = tmp[(v * o->ne + e) * o->nd + i];
@@ -778,7 +805,7 @@ int adgref_step(adgref* o, int n_steps) {
       memcpy(o->r, o->w, sizeof(double) * sz);
       for (int m = 0; m < o->stages; ++m) {
         stage_coeffs(o, m);
-        for (int64_t e = 0; e < o->ne; ++e) element_rhs(o, o->r, e, m, 1, o->kk);
+        all_elements_rhs(o, o->r, m, 1, o->kk);
         for (int64_t i = 0; i < sz; ++i) {
           if (m + 1 < o->stages) o->r[i] = o->w[i] + dt * o->rka[m] * o->kk[i];
           o->w[i] = o->w[i] + dt * o->rkb[m] * o->kk[i];
@@ -788,7 +815,7 @@ int adgref_step(adgref* o, int n_steps) {
       /* 2N scheme: q <- A_m q + dt k_m ; w <- w + B_m q */
       for (int m = 0; m < o->stages; ++m) {
         stage_coeffs(o, m);
-        for (int64_t e = 0; e < o->ne; ++e) element_rhs(o, o->w, e, m, 1, o->kk);
+        all_elements_rhs(o, o->w, m, 1, o->kk);
         for (int64_t i = 0; i < sz; ++i) {
           o->q[i] = (m == 0 ? 0.0 : o->rka[m] * o->q[i]) + dt * o->kk[i];
           o->w[i] = o->w[i] + o->rkb[m] * o->q[i];

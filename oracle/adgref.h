@@ -67,6 +67,9 @@ void adgref_set_state(adgref* o, const double* u);
 void adgref_get_state(const adgref* o, double* u);
 int adgref_step(adgref* o, int n_steps);
 void adgref_rhs(adgref* o, const double* u, double* k);
+/* Threads the element loops of adgref_rhs and adgref_step use: 1, or the OpenMP thread
+ * count in the all-cores build (compiled with -fopenmp; same results). */
+int adgref_threads(void);
 void adgref_rhs_elements(adgref* o, const double* u, const int64_t* elems, int64_t n_sel,
                          double* k);
 void adgref_conservation(const adgref* o, const double* u, double* sums);

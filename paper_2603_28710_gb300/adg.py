@@ -35,7 +35,7 @@ SYMBOLS = ["adg_default_options", "adg_create", "adg_set_state", "adg_init_vorte
            "adg_batch_destroy", "adg_mlp_num_params", "adg_mlp_grad", "adg_mlp_forward",
            "adg_mlp_adam", "adg_mlp_to_bf16", "adg_set_learned_model", "adg_set_trace_log",
            "adg_learned_samples", "adg_host_gauss", "adg_host_at_coeffs",
-           "adg_host_rk", "adg_host_schedule", "adg_host_num_interfaces"]
+           "adg_host_rk", "adg_host_schedule", "adg_host_num_interfaces", "adg_measure_peak"]
 
 
 class AdgError(RuntimeError):
@@ -120,6 +120,7 @@ def lib():
             "adg_host_rk": ([I, P, P, P, P], I),
             "adg_host_schedule": ([I, I, I, I, I, P, U64, I, I64, I, P, P, P], I),
             "adg_host_num_interfaces": ([I, P], I),
+            "adg_measure_peak": ([I, P, P], I),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -196,6 +197,17 @@ def host_schedule(flux, delay_mode, max_delay, np_, P, dim, seed, dmax, n0, coun
     return comm, k, dl[:, :nif]
 
 
+PEAK_KINDS = {"fp64_fma": 0, "fp32_fma": 1, "fp64_mma": 2, "fp64_fma+mma": 3, "fp32x2_fma": 4}
+
+
+def measure_peak(kind):
+    """Measured arithmetic rate of one instruction kind on the current device:
+    (TFLOP/s, ms of the timed launch).  Kinds: PEAK_KINDS."""
+    t, ms = ctypes.c_double(), ctypes.c_double()
+    _check(lib().adg_measure_peak(PEAK_KINDS[kind], ctypes.byref(t), ctypes.byref(ms)))
+    return t.value, ms.value
+
+
 def rhs_noalloc(dim, n_elem, degree, u, k, lo=None, hi=None, gamma=1.4, stream=None):
     """adg_rhs_noalloc on CUDA torch tensors u (read) and k (written); no allocation."""
     lo = lo if lo is not None else ((-5.0,) * dim)
@@ -210,10 +222,14 @@ def rhs_noalloc(dim, n_elem, degree, u, k, lo=None, hi=None, gamma=1.4, stream=N
     pk, nk, dk = _buf(k, writable=True)
     if not (du and dk) or n != nk:
         raise ValueError("u and k must be CUDA tensors of the same size")
-    if stream is None:
-        import torch
-        stream = torch.cuda.current_stream().cuda_stream
-    _check(lib().adg_rhs_noalloc(ctypes.byref(m), degree, gamma, pu, pk, n, stream))
+    if u.device != k.device:
+        raise ValueError("u and k must be on the same CUDA device")
+    import torch
+    # the library works on the current device: make it the tensors' device
+    with torch.cuda.device(u.device):
+        if stream is None:
+            stream = torch.cuda.current_stream(u.device).cuda_stream
+        _check(lib().adg_rhs_noalloc(ctypes.byref(m), degree, gamma, pu, pk, n, stream))
 
 
 # ---- solver ---------------------------------------------------------------------------

@@ -304,9 +304,33 @@ bool valid_degree(int dim, int degree) {
 
 size_t prec_bytes(int prec) { return storage_bytes(prec); }
 
-// Event pair around one launch (profiling only).
+// Folds the recorded event pairs into the per-kind totals and empties the pool (waits
+// for the solver's stream).
+cudaError_t prof_fold(adg_solver* s) {
+  cudaError_t err = cudaStreamSynchronize(s->stream);
+  if (err != cudaSuccess) return err;
+  for (size_t i = 0; i + 1 < s->ev_used; i += 2) {
+    float t = 0.f;
+    err = cudaEventElapsedTime(&t, s->ev_pool[i], s->ev_pool[i + 1]);
+    if (err != cudaSuccess) return err;
+    const int kind = s->ev_kind[i / 2];
+    s->prof_ms[kind] += t;
+    s->prof_n[kind] += 1;
+  }
+  s->ev_used = 0;
+  return cudaSuccess;
+}
+
+// Event pair around one launch (profiling only).  The pool holds at most kMaxProfEvents
+// events: when it is full the recorded pairs are folded into running totals (one wait
+// for the stream), so a long profiled run keeps a bounded number of CUDA events.
+constexpr size_t kMaxProfEvents = 2048;
 cudaError_t prof_begin(adg_solver* s, int kind) {
   if (!s->profiling) return cudaSuccess;
+  if (s->ev_used + 2 > kMaxProfEvents) {
+    cudaError_t err = prof_fold(s);
+    if (err != cudaSuccess) return err;
+  }
   if (s->ev_used + 2 > s->ev_pool.size()) {
     for (int i = 0; i < 64; ++i) {
       cudaEvent_t e;
@@ -1094,23 +1118,21 @@ adg_status adg_set_profiling(adg_solver* s, int enable) {
   if (!s) return fail(nullptr, ADG_ERR_INVALID, "handle is NULL");
   s->profiling = enable != 0;
   s->ev_used = 0;
+  s->prof_ms[0] = s->prof_ms[1] = 0.0;
+  s->prof_n[0] = s->prof_n[1] = 0;
   return ADG_OK;
 }
 
 adg_status adg_get_profile(adg_solver* s, double* ms, int64_t* launches) {
   if (!s) return fail(nullptr, ADG_ERR_INVALID, "handle is NULL");
   if (!ms || !launches) return fail(s, ADG_ERR_INVALID, "ms or launches is NULL");
-  ms[0] = ms[1] = 0.0;
-  launches[0] = launches[1] = 0;
-  ADG_CUDA(s, cudaStreamSynchronize(s->stream));
-  for (size_t i = 0; i + 1 < s->ev_used; i += 2) {
-    float t = 0.f;
-    ADG_CUDA(s, cudaEventElapsedTime(&t, s->ev_pool[i], s->ev_pool[i + 1]));
-    int kind = s->ev_kind[i / 2];
-    ms[kind] += t;
-    launches[kind] += 1;
+  ADG_CUDA(s, prof_fold(s));
+  for (int kind = 0; kind < 2; ++kind) {
+    ms[kind] = s->prof_ms[kind];
+    launches[kind] = s->prof_n[kind];
+    s->prof_ms[kind] = 0.0;
+    s->prof_n[kind] = 0;
   }
-  s->ev_used = 0;
   return ADG_OK;
 }
 

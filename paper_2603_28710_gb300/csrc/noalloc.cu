@@ -36,6 +36,20 @@ adg_status noalloc_fail(adg_status st, const std::string& m) {
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
+// The operator tables travel as a kernel argument (kernel arguments may hold up to 32 KB;
+// the tables take about 9 KB) and a one-block kernel stores them into the scratch array:
+// the launch copies the argument when it is enqueued, so no host memory is read after the
+// call returns and no host-to-device copy waits for the stream.
+struct TableBlob {
+  unsigned long long v[sizeof(adg::OpTables) / 8];
+};
+static_assert(sizeof(adg::OpTables) % 8 == 0, "tables are a whole number of 8-byte words");
+static_assert(sizeof(TableBlob) <= 30 * 1024, "tables must fit in a kernel argument");
+
+__global__ void store_tables_kernel(const TableBlob T, unsigned long long* dst) {
+  for (int i = threadIdx.x; i < (int)(sizeof(TableBlob) / 8); i += blockDim.x) dst[i] = T.v[i];
+}
+
 }  // namespace
 
 extern "C" adg_status adg_rhs_noalloc(const adg_mesh* mesh, int degree, double gamma,
@@ -94,8 +108,11 @@ extern "C" adg_status adg_rhs_noalloc(const adg_mesh* mesh, int degree, double g
   OpTables* tab_dev = reinterpret_cast<OpTables*>(base);
   void* tr = base + tab_bytes;
   void* fl = base + tab_bytes + tr_bytes;
-  e = cudaMemcpyAsync(tab_dev, &tab, sizeof(OpTables), cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return noalloc_fail(ADG_ERR_CUDA, std::string("table upload: ") + cudaGetErrorString(e));
+  TableBlob blob;
+  std::memcpy(blob.v, &tab, sizeof(OpTables));
+  store_tables_kernel<<<1, 128, 0, s>>>(blob, reinterpret_cast<unsigned long long*>(tab_dev));
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return noalloc_fail(ADG_ERR_CUDA, std::string("table store: ") + cudaGetErrorString(e));
 
   MeshArgs m;
   std::memset(&m, 0, sizeof(m));

@@ -1,0 +1,160 @@
+// Arithmetic peak probes (adg_measure_peak in include/adg.h): the rates that bound the
+// operator kernels, measured on the GPU the library runs on instead of taken from a data
+// sheet.  Each probe keeps every warp slot busy with independent dependency chains of one
+// instruction kind and times launches of about 50 ms with CUDA events (best of three, after
+// a warm-up launch).
+//
+//   kind 0  FP64 FMA (DFMA):               8 independent chains per thread
+//   kind 1  FP32 FMA (FFMA):               8 independent chains per thread
+//   kind 2  FP64 tensor MMA (DMMA):        mma.sync m8n8k4 f64, 4 independent accumulators per warp
+//   kind 3  DFMA and DMMA together:        even warps run kind 0, odd warps kind 2
+//   kind 4  packed FP32x2 FMA (FFMA2):     8 independent chains of float2 per thread
+//
+// Kind 3 tells whether the FP64 tensor path adds throughput to the FP64 FMA pipe (its rate
+// is then close to the sum of kinds 0 and 2) or shares it (close to either alone).
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "../../include/adg.h"
+
+namespace adg {
+void noalloc_set_error(const char* msg);  // per-thread error text (host.cu)
+}
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kChains = 8;
+
+__device__ __forceinline__ void dfma_chains(double (&a)[kChains], double b, double c, int iters) {
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < kChains; ++j) a[j] = fma(a[j], b, c);
+  }
+}
+
+__device__ __forceinline__ void dmma_chains(double (&acc)[4][2], double a, double b, int iters) {
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      asm volatile(
+          "mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};"
+          : "+d"(acc[j][0]), "+d"(acc[j][1])
+          : "d"(a), "d"(b));
+  }
+}
+
+// The results feed a store that never happens for these inputs (|a| stays below 2), so
+// the compiler keeps every operation.
+__global__ void __launch_bounds__(kThreads) probe_kernel(int kind, int iters, double seed,
+                                                         double* sink) {
+  const int warp = threadIdx.x >> 5;
+  const bool use_mma = kind == 2 || (kind == 3 && (warp & 1));
+  if (kind == 1) {
+    float a[kChains];
+#pragma unroll
+    for (int j = 0; j < kChains; ++j) a[j] = (float)seed * (j + 1) + threadIdx.x * 1e-7f;
+    const float b = 0.999999f, c = 1e-7f;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+      for (int j = 0; j < kChains; ++j) a[j] = fmaf(a[j], b, c);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < kChains; ++j) s += a[j];
+    if (s > 1e30f) sink[blockIdx.x] = s;
+  } else if (kind == 4) {
+    float2 a[kChains];
+#pragma unroll
+    for (int j = 0; j < kChains; ++j)
+      a[j] = make_float2((float)seed * (j + 1), (float)seed * (j + 2) + threadIdx.x * 1e-7f);
+    const float2 b = make_float2(0.999999f, 0.999998f), c = make_float2(1e-7f, 2e-7f);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+      for (int j = 0; j < kChains; ++j) a[j] = __ffma2_rn(a[j], b, c);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < kChains; ++j) s += a[j].x + a[j].y;
+    if (s > 1e30f) sink[blockIdx.x] = s;
+  } else if (use_mma) {
+    double acc[4][2];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[j][0] = acc[j][1] = seed * (j + 1);
+    dmma_chains(acc, 1e-3, 0.999, iters / 4);  // 4 MMAs per iteration, each 512 flops per warp
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) s += acc[j][0] + acc[j][1];
+    if (s > 1e300) sink[blockIdx.x] = s;
+  } else {
+    double a[kChains];
+#pragma unroll
+    for (int j = 0; j < kChains; ++j) a[j] = seed * (j + 1) + threadIdx.x * 1e-9;
+    dfma_chains(a, 0.999999, 1e-9, iters);
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < kChains; ++j) s += a[j];
+    if (s > 1e300) sink[blockIdx.x] = s;
+  }
+}
+
+// flops of one launch: per FMA thread 2 * kChains * iters (FP32x2: twice that); per MMA
+// warp (iters / 4) * 4 * 512
+double launch_flops(int kind, int blocks, int iters) {
+  const double warps = (double)blocks * (kThreads / 32);
+  const double fma_warp = 32.0 * 2.0 * kChains * iters;
+  const double mma_warp = (double)(iters / 4) * 4 * 512.0;
+  switch (kind) {
+    case 0: case 1: return warps * fma_warp;
+    case 4: return warps * fma_warp * 2.0;
+    case 2: return warps * mma_warp;
+    case 3: return warps / 2 * (fma_warp + mma_warp);
+  }
+  return 0.0;
+}
+
+adg_status probe_fail(adg_status st, const std::string& m) {
+  adg::noalloc_set_error(m.c_str());
+  return st;
+}
+
+}  // namespace
+
+extern "C" adg_status adg_measure_peak(int kind, double* tflops, double* ms) {
+  if (kind < 0 || kind > 4 || !tflops) return probe_fail(ADG_ERR_INVALID, "bad peak-probe arguments");
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return probe_fail(ADG_ERR_CUDA, std::string("device query: ") + cudaGetErrorString(e));
+  // four blocks of 256 threads per SM: 32 warps per SM, eight per sub-partition
+  const int blocks = sms * 4;
+  // about 50 ms per launch at the nominal rates (FP64 1.25, FP32 75 TFLOP/s)
+  const int iters = (kind == 1) ? 1500000 : (kind == 4 ? 750000 : 25000);
+  double* sink = nullptr;
+  cudaStream_t s = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&sink, (size_t)blocks * sizeof(double));
+  float best = 0.f;
+  for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {  // first launch is a warm-up
+    e = cudaEventRecord(e0, s);
+    if (e == cudaSuccess) probe_kernel<<<blocks, kThreads, 0, s>>>(kind, iters, 0.5, sink);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    if (e == cudaSuccess && rep > 0 && (best == 0.f || t < best)) best = t;
+  }
+  if (sink) cudaFree(sink);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (s) cudaStreamDestroy(s);
+  if (e != cudaSuccess) return probe_fail(ADG_ERR_CUDA, std::string("peak probe: ") + cudaGetErrorString(e));
+  *tflops = launch_flops(kind, blocks, iters) / (best * 1e-3) / 1e12;
+  if (ms) *ms = best;
+  return ADG_OK;
+}

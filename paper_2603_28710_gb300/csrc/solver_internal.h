@@ -66,6 +66,8 @@ struct adg_solver {
   std::vector<cudaEvent_t> ev_pool;
   std::vector<int> ev_kind;  // kind of each recorded pair
   size_t ev_used = 0;
+  double prof_ms[2] = {0.0, 0.0};  // totals folded from the pool when it filled up
+  int64_t prof_n[2] = {0, 0};
 };
 
 namespace adg {

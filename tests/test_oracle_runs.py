@@ -137,3 +137,17 @@ def test_random_state_run_is_finite_and_conservative():
     u = o.get_state()
     assert np.isfinite(u).all()
     assert np.abs(o.conservation(u) - o.conservation(u0)).max() < 1e-13
+
+
+def test_all_cores_build_equals_single_threaded_bitwise():
+    # the OpenMP variant (timing only) splits elements over threads; each element's
+    # arithmetic is unchanged, so runs and residuals agree bit for bit
+    kw = dict(n_elem=(16, 16), degree=3, P=(4, 4), max_delay=3, flux="at", rk="ck45", dt=2e-3)
+    a, b = O.Oracle(**kw), O.Oracle(parallel=True, **kw)
+    u0 = a.init_vortex()
+    for o in (a, b):
+        o.set_state(u0)
+        o.step(9)
+    assert np.array_equal(a.get_state(), b.get_state())
+    assert np.array_equal(a.rhs(u0), b.rhs(u0))
+    assert O.threads(False) == 1 and O.threads(True) >= 1

@@ -4,12 +4,14 @@ Some callers own the whole device memory budget (a fixed arena or pool) or run a
 where cudaMalloc's implicit synchronisation is not allowed; adg_rhs_noalloc serves them
 from a built-in device scratch array instead of allocating.  These tests call it through
 the C ABI and compare it with the handle-based operator adg_rhs, on two calls in a row
-with different inputs (so a stale scratch would show).  The file sorts last so that a
+with different inputs (so a stale scratch would show), and with the CPU oracle's operator
+(dense quadrature of Eq. 6, mass solve of Eq. 7) on the same inputs.  The file sorts last so that a
 failure here cannot hide any other test.
 """
 import numpy as np
 import pytest
 
+import oracle as O
 from paper_2603_28710_gb300 import adg
 from paper_2603_28710_gb300.inputs import random_state
 
@@ -38,6 +40,7 @@ def rel(a, b):
 def test_noalloc_matches_rhs_on_two_calls_in_a_row(dim, n_elem, p, lo, hi):
     import torch
     s = adg.Solver(dim=dim, n_elem=n_elem, degree=p, lo=lo, hi=hi, dt=1e-3)
+    o = O.Oracle(dim=dim, n_elem=n_elem, degree=p, lo=lo, hi=hi, dt=1e-3)
     for seed in (1, 2):
         u = torch.from_numpy(random_state(s.shape, dim, seed=seed)).cuda()
         k_ref = torch.empty_like(u)
@@ -47,6 +50,8 @@ def test_noalloc_matches_rhs_on_two_calls_in_a_row(dim, n_elem, p, lo, hi):
         torch.cuda.synchronize()
         assert torch.isfinite(k).all()
         assert rel(k, k_ref) < TOL
+        ko = torch.from_numpy(o.rhs(u.cpu().numpy()))
+        assert rel(k.cpu(), ko) < TOL
     s.close()
 
 
