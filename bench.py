@@ -12,13 +12,17 @@ steps, 3 delayed ones), i.e. 40 RK stages over 6,553,600 DoF.
 
 Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank runs an independent
 replica on its own GPU ("replicas only": the path has no exchange between GPUs).
-Besides the headline (value, e2e through the C ABI with pinned host buffers, roofline of
-the volume kernel from live CUDA events, clocks sampled by nvidia-smi, the oracle's CPU
-throughput, launch count) the line carries:
+Besides the headline (value from CUDA events around whole benchmark steps with no per-launch
+events inside the timed region, e2e through the C ABI with pinned host buffers, roofline of
+the volume kernel from the library's per-launch events in a separate pass, clocks sampled
+by nvidia-smi, the oracle's CPU throughput on all host cores and on one, launch count, the
+arithmetic rates measured on this GPU) the line carries:
   variants         the same workload with the FP64, FP32-pair and FP32 operators, with
-                   their L2 errors against the exact vortex;
+                   their L2 errors against the exact vortex, and with the standard delayed
+                   flux and the seeded random-delay mode;
   batched          64 uneven vortex instances in one CUDA graph per step vs separate handles;
-  taylor_green_3d  the 3D Taylor-Green vortex (64^3, p = 3) in each operator arithmetic;
+  taylor_green_3d  the 3D Taylor-Green vortex (64^3, p = 3) in each operator arithmetic, with
+                   its own roofline, end-to-end figure and oracle CPU baseline;
   learned_ghost    the learned ghost-trace predictor against plain AT on its 3D case.
 `--impl reference` times the CPU oracle on the same workload instead (rank 0 only).
 """
@@ -179,38 +183,74 @@ class ClockSampler:
 
 
 # ---- oracle CPU baseline ---------------------------------------------------------------
-def make_oracle():
-    """The CPU oracle on the full-size workload with the CFL-0.1 time step."""
+def make_oracle(parallel=False):
+    """The CPU oracle on the full-size workload with the CFL-0.1 time step (parallel: the
+    all-cores build, OpenMP over elements, same results)."""
     import oracle
     o = oracle.Oracle(n_elem=(N_ELEM, N_ELEM), degree=DEGREE, P=(P, P), max_delay=L, flux="at",
                       rk="ck45", dt=1.0)
     u0 = o.init_vortex()
     dt = o.dt_from_cfl(u0, CFL, 0.0)
     o = oracle.Oracle(n_elem=(N_ELEM, N_ELEM), degree=DEGREE, P=(P, P), max_delay=L, flux="at",
-                      rk="ck45", dt=dt)
+                      rk="ck45", dt=dt, parallel=parallel)
     o.set_state(u0)
     return o
 
 
-def oracle_sample(time_steps):
+def cpu_model():
+    """CPU model name of this host (lscpu, else /proc/cpuinfo, else platform)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def oracle_sample(time_steps, parallel=False):
     """Times the CPU oracle on the full-size workload for a few time steps; returns
-    (GDoF-RK-stages/s, seconds)."""
-    o = make_oracle()
+    (GDoF-RK-stages/s, seconds, threads)."""
+    import oracle
+    o = make_oracle(parallel)
     t0 = time.perf_counter()
     o.step(time_steps)
     sec = time.perf_counter() - t0
     ndof = 4 * N_ELEM * N_ELEM * (DEGREE + 1) ** 2
-    return ndof * 5 * time_steps / sec / 1e9, sec
+    return ndof * 5 * time_steps / sec / 1e9, sec, oracle.threads(parallel)
+
+
+def cpu_baseline_2d(steps_all, steps_single):
+    """The oracle on the bench workload: all host cores (OpenMP over elements, the
+    reported value) and one core, with the CPU model."""
+    v, sec, thr = oracle_sample(steps_all, parallel=True)
+    v1, sec1, _ = oracle_sample(steps_single, parallel=False)
+    return {"value": v, "unit": METRIC, "cores": thr, "kind": "oracle",
+            "sample": f"{steps_all} RK time steps (5 stages each) of the full 256^2 p=4 workload, "
+                      f"C oracle with OpenMP over elements on {thr} threads, {sec:.1f} s",
+            "cpu_model": cpu_model(), "nproc": os.cpu_count(),
+            "single_thread": {"value": v1, "cores": 1,
+                              "sample": f"{steps_single} RK time steps, one thread, {sec1:.1f} s"}}
 
 
 def run_reference(args, rank, world):
-    """The oracle as the reference arm, single-threaded on the host cores (rank 0 only).
+    """The oracle as the reference arm, on all host cores (OpenMP over elements; rank 0 only).
     Each step is a bounded sample of the workload: one RK time step (5 stages), or one
     stage (one operator evaluation) when K time steps would take more than about two
     minutes."""
     if rank != 0:
         return
-    o = make_oracle()
+    import oracle
+    o = make_oracle(parallel=True)
+    threads = oracle.threads(True)
     o.step(args.warmup)
     ndof = 4 * N_ELEM * N_ELEM * (DEGREE + 1) ** 2
     t0 = time.perf_counter()
@@ -234,9 +274,10 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config("fp64"),
-            "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": threads, "kind": "oracle",
                              "sample": f"{sample} of the full 256^2 p=4 workload per step, "
-                                       "single-threaded C oracle"},
+                                       f"C oracle with OpenMP over elements on {threads} threads",
+                             "cpu_model": cpu_model(), "nproc": os.cpu_count()},
             "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -258,12 +299,48 @@ def whole_job_value(work_per_rank_per_step, steps, seconds_max, world):
     return world * work_per_rank_per_step * steps / seconds_max / 1e9
 
 
-def variant_run(adg, stream, precision, steps_per, k, warm, dt):
-    """Throughput and L2 error vs the exact vortex of one operator arithmetic on the bench
-    workload (fixed dt, same initial state)."""
+def roofline_line(precision, D, N, ndof, vol_ms, vol_n, mpk, kernel):
+    """Roofline of the volume/update kernel from its average launch time: algorithmic
+    flops (FP64 form, bound by the FP64 pipe) or algorithmic HBM bytes (FP32 and FP32-pair
+    forms) per launch over the average launch duration, against the rates measured on this
+    GPU (adg_measure_peak) and MEASURED_PEAKS.json's copy bandwidth."""
+    nodes = ndof // (D + 2)
+    avg_s = vol_ms * 1e-3 / max(vol_n, 1)
+    flops = vol_flops_per_node(D, N) * nodes
+    byts = np.mean([vol_bytes_per_dof_stage(m, 5, Q_BYTES[precision]) for m in range(5)]) * ndof
+    pk = peaks()
+    hbm = pk.get("hbm_gbs", 6800.0)
+    hbm_src = "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in pk else "fallback 6.8 TB/s"
+    fp64 = mpk.get("fp64_fma")
+    hbm_view = {"achieved_gbs": byts / avg_s / 1e9, "peak_gbs": hbm, "frac": byts / avg_s / 1e9 / hbm}
+    alu_view = {"achieved_tflops": flops / avg_s / 1e12, "fp64_fma_peak_tflops": fp64,
+                "frac_of_fp64": (flops / avg_s / 1e12 / fp64) if fp64 else None}
+    if precision == "fp64":
+        roof = {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": fp64 or 1.25,
+                "unit": "TFLOP/s",
+                "peak_source": ("FP64 FMA rate measured in this run by adg_measure_peak (nominal 1.25)"
+                                if fp64 else "nominal FP64 1.25 TFLOP/s")}
+    else:
+        roof = {"bound": "hbm", "achieved": byts / avg_s / 1e9, "peak": hbm, "unit": "GB/s",
+                "peak_source": hbm_src}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["kernel"] = kernel
+    roof["avg_launch_ms"] = avg_s * 1e3
+    roof["algorithmic_bytes_per_launch"] = byts
+    roof["algorithmic_flops_per_launch"] = flops
+    roof["hbm_view"] = hbm_view
+    roof["alu_view"] = alu_view
+    return roof
+
+
+def variant_run(adg, stream, precision, steps_per, k, warm, dt, flux="at", delay_mode="caa",
+                at_np=0):
+    """Throughput and L2 error vs the exact vortex of one operator arithmetic (and one
+    subdomain-face rule) on the bench workload (fixed dt, same initial state)."""
     import torch
-    s = adg.Solver(n_elem=(N_ELEM, N_ELEM), degree=DEGREE, P=(P, P), max_delay=L, flux="at",
-                   rk="ck45", dt=dt, precision=precision, stream=stream.cuda_stream)
+    s = adg.Solver(n_elem=(N_ELEM, N_ELEM), degree=DEGREE, P=(P, P), max_delay=L, flux=flux,
+                   rk="ck45", dt=dt, precision=precision, delay_mode=delay_mode,
+                   random_delay_max=2, seed=20260301, at_np=at_np, stream=stream.cuda_stream)
     s.init_vortex()
     s.step(steps_per * warm)
     torch.cuda.synchronize()
@@ -279,12 +356,31 @@ def variant_run(adg, stream, precision, steps_per, k, warm, dt):
     s.set_profiling(False)
     ndof = 4 * N_ELEM * N_ELEM * (DEGREE + 1) ** 2
     info = s.info()
-    err = s.l2_error_vortex(info["t"])  # after warm + k + 2 benchmark steps
+    finite = s.check_finite()
+    err = s.l2_error_vortex(info["t"]) if finite else None  # after warm + k + 2 bench steps
     s.close()
     return {"value": ndof * 5 * steps_per * k / (ms * 1e-3) / 1e9, "l2_flush": False,
             "vol_ms_per_launch": prof["vol"][0] / max(prof["vol"][1], 1),
             "flux_ms_per_launch": prof["flux"][0] / max(prof["flux"][1], 1),
-            "l2_error_vs_exact": [float(x) for x in err], "t": info["t"]}
+            "finite": bool(finite),
+            "l2_error_vs_exact": [float(x) for x in err] if finite else None, "t": info["t"]}
+
+
+def delay_mode_runs(adg, stream, steps_per, k, dt):
+    """The bench workload (FP64 operator) under the other subdomain-face rules of the
+    256^2 p=4 configuration: the standard delayed flux (Algorithm 2, CAA L=3) and seeded
+    random delays in {0, 1, 2} (seed 20260301) with the AT and the standard flux."""
+    out = {}
+    for name, flux, mode, at_np in (("std_caa", "std", "caa", 0), ("at_random_np2", "at", "random", 2),
+                                    ("std_random", "std", "random", 0),
+                                    ("at_random_np4", "at", "random", 4)):
+        out[name] = variant_run(adg, stream, "fp64", steps_per, k, 2, dt, flux=flux, delay_mode=mode,
+                                at_np=at_np)
+    out["workload"] = ("256^2 p=4 vortex, 8x8 subdomains, CK4(5), CFL 0.1 time step, FP64 operator; "
+                       "std_caa: Algorithm 2 with L=3; *_random: per-interface delays in {0,1,2}; "
+                       "AT with N_p=2 (three levels) and N_p=4 (five levels: the extrapolation over "
+                       "random delays diverges at this CFL number, in the oracle too)")
+    return out
 
 
 def batched_run(adg, stream, k=6):
@@ -337,49 +433,105 @@ def batched_run(adg, stream, k=6):
             "autotune_s": tune_s}
 
 
-def tgv_run(adg, stream, k=3, total_steps=100):
+TGV_N, TGV_DEGREE, TGV_P, TGV_L = 64, 3, 8, 4
+
+
+def tgv_solver(adg, stream, prec, dt=0.0):
+    return adg.Solver(dim=3, n_elem=(TGV_N,) * 3, degree=TGV_DEGREE, lo=(0, 0, 0),
+                      hi=(2 * np.pi,) * 3, P=(TGV_P,) * 3, max_delay=TGV_L, flux="at", rk="ck45",
+                      cfl=0.1, dt=dt, precision=prec, stream=stream.cuda_stream)
+
+
+def tgv_cpu_baseline(sample_elems=2048):
+    """The oracle on the 3D workload: one full operator evaluation (one RK stage's right-hand
+    side over all 262,144 elements) on all host cores, and one core on a sample of elements."""
+    import oracle
+    kw = dict(dim=3, n_elem=(TGV_N,) * 3, degree=TGV_DEGREE, lo=(0, 0, 0), hi=(2 * np.pi,) * 3,
+              dt=1e-3)
+    ndof = 5 * TGV_N ** 3 * (TGV_DEGREE + 1) ** 3
+    o = oracle.Oracle(parallel=True, **kw)
+    u = o.init_tgv(0.1)
+    t0 = time.perf_counter()
+    o.rhs(u)
+    sec = time.perf_counter() - t0
+    thr = oracle.threads(True)
+    o1 = oracle.Oracle(**kw)
+    sel = np.random.default_rng(3).integers(0, TGV_N ** 3, sample_elems)
+    t0 = time.perf_counter()
+    o1.rhs_elements(u, sel)
+    sec1 = time.perf_counter() - t0
+    v1 = ndof * sample_elems / TGV_N ** 3 / sec1 / 1e9
+    return {"value": ndof / sec / 1e9, "unit": METRIC, "cores": thr, "kind": "oracle",
+            "sample": f"one operator evaluation (one RK stage) over the full 64^3 p=3 mesh, C oracle "
+                      f"with OpenMP over elements on {thr} threads, {sec:.1f} s",
+            "cpu_model": cpu_model(), "nproc": os.cpu_count(),
+            "single_thread": {"value": v1, "cores": 1,
+                              "sample": f"operator on {sample_elems} sampled elements, one thread, "
+                                        f"{sec1:.1f} s"}}
+
+
+def tgv_run(adg, stream, mpk, flush, k=3, total_steps=100, with_cpu=True):
     """3D Taylor-Green vortex, 64^3 hexes, p = 3, 8x8x8 subdomains, L = 4, AT flux,
     CK4(5), CFL 0.1: throughput per operator arithmetic (one benchmark step = one schedule
-    cycle of L + N_p + 1 = 8 time steps), and after total_steps RK steps from the initial
-    condition each form's relative L2 difference from the FP64 form and its drift of the
-    conserved totals (mass, momentum, energy; max over variables, relative)."""
+    cycle of L + N_p + 1 = 8 time steps; the 671 MB state exceeds L2, so no flush is needed),
+    per-kernel times from a separate profiled pass, the roofline of the volume kernel, and
+    after total_steps RK steps from the initial condition each form's relative L2 difference
+    from the FP64 form and its drift of the conserved totals (mass, momentum, energy; max
+    over variables, relative).  The FP64 form also gets an end-to-end figure through the
+    C ABI (pinned host state in, 8 steps, state out) and the oracle's CPU baseline."""
     import torch
     out = {}
-    ndof = 5 * 64 ** 3 * 4 ** 3
+    ndof = 5 * TGV_N ** 3 * (TGV_DEGREE + 1) ** 3
+    work = ndof * 5 * 8
     u64 = None
     for prec in ("fp64", "df64", "fp32"):
-        s = adg.Solver(dim=3, n_elem=(64, 64, 64), degree=3, lo=(0, 0, 0), hi=(2 * np.pi,) * 3,
-                       P=(8, 8, 8), max_delay=4, flux="at", rk="ck45", cfl=0.1, precision=prec,
-                       stream=stream.cuda_stream)
+        s = tgv_solver(adg, stream, prec)
         s.init_tgv(0.1)
         c0 = s.conservation()
         s.step(8)
         torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        s.step(8 * k)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        s.set_profiling(True)
-        s.step(8)
-        prof = s.get_profile()
-        s.set_profiling(False)
+        ms = sum(timed_steps(s, stream, k, 8, flush))
+        prof = profiled_pass(s, stream, 1, 8, flush)
         s.step(total_steps - 8 * (k + 2))
         u = s.get_state()
         c1 = s.conservation()
+        dt = s.info()["dt"]
         s.close()
-        out[prec] = {"value": ndof * 5 * 8 * k / (ms * 1e-3) / 1e9,
-                     "vol_ms_per_launch": prof["vol"][0] / max(prof["vol"][1], 1),
+        vol_ms, vol_n = prof["vol"]
+        out[prec] = {"value": work * k / (ms * 1e-3) / 1e9,
+                     "vol_ms_per_launch": vol_ms / max(vol_n, 1),
                      "flux_ms_per_launch": prof["flux"][0] / max(prof["flux"][1], 1),
+                     "roofline": roofline_line(prec, 3, TGV_DEGREE + 1, ndof, vol_ms, vol_n, mpk,
+                                               "vol_kernel<3,4>"),
                      f"conservation_drift_after_{total_steps}_steps":
                          float(np.max(np.abs(c1 - c0)) / np.max(np.abs(c0)))}
         if prec == "fp64":
             u64 = u
+            # end to end through the public API with pinned host buffers
+            host_in = torch.from_numpy(u).pin_memory()
+            host_out = torch.empty_like(host_in).pin_memory()
+            s2 = tgv_solver(adg, stream, prec, dt=dt)
+            s2.set_state(host_in)
+            s2.step(8)
+            s2.get_state(host_out)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(2):
+                s2.set_state(host_in)
+                s2.step(8)
+                s2.get_state(host_out)
+            torch.cuda.synchronize()
+            e2e_sec = time.perf_counter() - t0
+            s2.close()
+            out[prec]["e2e"] = {"value": work * 2 / e2e_sec / 1e9, "unit": METRIC,
+                                "h2d_bytes_per_step": ndof * 8, "d2h_bytes_per_step": ndof * 8}
+            del host_in, host_out
         else:
             out[prec][f"rel_l2_diff_vs_fp64_after_{total_steps}_steps"] = float(
                 np.linalg.norm(u - u64) / np.linalg.norm(u64))
         del u
+    if with_cpu:
+        out["cpu_baseline"] = tgv_cpu_baseline()
     out["workload"] = ("3D Taylor-Green vortex 64^3 hexes p=3 (83.9M DoF), 8x8x8 subdomains, "
                        "CAA L=4, AT flux, CK4(5), CFL 0.1")
     out["unit"] = METRIC
@@ -436,6 +588,42 @@ def learned_run(adg, stream, k=2, err_steps=24):
 
 
 # ---- GPU arm -----------------------------------------------------------------------------
+def measured_peaks(adg):
+    """Arithmetic rates of this GPU from the library's probe (adg_measure_peak), TFLOP/s,
+    with the SM clock seen during each probe."""
+    out = {"sm_mhz": {}}
+    for kind in ("fp64_fma", "fp64_mma", "fp64_fma+mma", "fp32_fma", "fp32x2_fma"):
+        t, _, mhz = adg.measure_peak(kind)
+        out[kind] = t
+        out["sm_mhz"][kind] = mhz
+    return out
+
+
+def timed_steps(s, stream, steps, steps_per, flush):
+    """Device time (ms) of `steps` benchmark steps, each bracketed by CUDA events on the
+    solver's stream, the L2 flushed before each step outside the events."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for i in range(steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        s.step(steps_per)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def profiled_pass(s, stream, steps, steps_per, flush):
+    """Per-kernel device times from the library's own events, in a pass of its own after
+    the timed region (the timed region runs without them)."""
+    s.set_profiling(True)
+    timed_steps(s, stream, steps, steps_per, flush)
+    prof = s.get_profile()
+    s.set_profiling(False)
+    return prof
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
     from paper_2603_28710_gb300 import adg, build
@@ -451,6 +639,7 @@ def run_gpu(args, rank, world, local_rank):
     steps_per = L + DEGREE + 1
     ndof = 4 * N_ELEM * N_ELEM * (DEGREE + 1) ** 2
     work = ndof * 5 * steps_per  # DoF-stages per benchmark step
+    mpk = measured_peaks(adg) if rank == 0 else {}
 
     s = adg.Solver(n_elem=(N_ELEM, N_ELEM), degree=DEGREE, P=(P, P), max_delay=L, flux="at",
                    rk="ck45", cfl=CFL, precision=args.precision, stream=stream.cuda_stream)
@@ -466,27 +655,19 @@ def run_gpu(args, rank, world, local_rank):
         s.step(steps_per)
     torch.cuda.synchronize()
 
-    # device-timed region: K steps, L2 flushed between them (outside the events)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
+    # device-timed region: K steps, L2 flushed between them (outside the events), no
+    # per-launch events inside it
     gpu_idx = os.environ.get("CUDA_VISIBLE_DEVICES", str(local_rank)).split(",")[local_rank] \
         if os.environ.get("CUDA_VISIBLE_DEVICES") else str(local_rank)
     barrier()
     torch.cuda.synchronize()
-    s.set_profiling(True)
     with ClockSampler(gpu_idx) as clk:
-        for i in range(args.steps):
-            flush.fill_(float(i))
-            ev[i][0].record(stream)
-            s.step(steps_per)
-            ev[i][1].record(stream)
-        torch.cuda.synchronize()
+        ms_list = timed_steps(s, stream, args.steps, steps_per, flush)
     barrier()
-    prof = s.get_profile()
-    s.set_profiling(False)
-    ms_list = [a.elapsed_time(b) for a, b in ev]
     ms = reduce_max(sum(ms_list), dev)
     value = whole_job_value(work, args.steps, ms * 1e-3, world)
+    # per-kernel times in a separate profiled pass of the same workload
+    prof = profiled_pass(s, stream, args.profile_steps, steps_per, flush)
 
     # end to end through the public API: pinned host state in, 8 steps, state out
     host_in = torch.from_numpy(s.get_state()).pin_memory()
@@ -509,43 +690,21 @@ def run_gpu(args, rank, world, local_rank):
     e2e_sec = reduce_max(time.perf_counter() - t0, dev)
     e2e_value = whole_job_value(work, args.steps, e2e_sec, world)
     state_bytes = ndof * 8
+    s2.close()
 
     if rank != 0:
         return
 
-    # roofline of the dominant kernel (volume/update kernel), timed live above
+    # roofline of the dominant kernel (volume/update kernel)
     vol_ms, vol_n = prof["vol"]
     flux_ms, flux_n = prof["flux"]
-    vol_avg_s = vol_ms * 1e-3 / max(vol_n, 1)
-    nodes = N_ELEM * N_ELEM * (DEGREE + 1) ** 2
-    flops_launch = vol_flops_per_node() * nodes
-    bytes_launch = np.mean([vol_bytes_per_dof_stage(m, 5, Q_BYTES[args.precision])
-                            for m in range(5)]) * ndof
-    pk = peaks()
-    fp64_peak_tflops = 1.25  # nominal GB300 FP64 rate (no FP64 tensor advantage)
-    if args.precision == "fp64":
-        roof = {"bound": "alu", "achieved": flops_launch / vol_avg_s / 1e12,
-                "peak": fp64_peak_tflops, "unit": "TFLOP/s",
-                "peak_source": "nominal FP64 1.25 TFLOP/s (recipe table); 1.19 measured by an FMA probe"}
-    else:
-        roof = {"bound": "hbm", "achieved": bytes_launch / vol_avg_s / 1e9,
-                "peak": pk.get("hbm_gbs", 6800.0), "unit": "GB/s",
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in pk else "fallback 6.8 TB/s"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["kernel"] = "vol_kernel<2,5>"
+    roof = roofline_line(args.precision, 2, DEGREE + 1, ndof, vol_ms, vol_n, mpk, "vol_kernel<2,5>")
     roof["traffic"] = ncu_traffic(args.precision)
-    roof["algorithmic_bytes_per_launch"] = bytes_launch
-    roof["algorithmic_flops_per_launch"] = flops_launch
-    roof["hbm_view"] = {"achieved_gbs": bytes_launch / vol_avg_s / 1e9,
-                        "peak_gbs": pk.get("hbm_gbs", 6800.0),
-                        "frac": bytes_launch / vol_avg_s / 1e9 / pk.get("hbm_gbs", 6800.0)}
+    launches_per_step = (vol_n + flux_n) / max(args.profile_steps, 1)
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        v, sec = oracle_sample(args.cpu_steps)
-        cpu = {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle",
-               "sample": f"{args.cpu_steps} RK time steps (5 stages each) of the full 256^2 p=4 "
-                         f"workload, single-threaded C oracle, {sec:.1f} s"}
+        cpu = cpu_baseline_2d(args.cpu_steps, args.cpu_steps_single)
 
     variants = None
     if world == 1 and not args.no_variants:
@@ -566,13 +725,14 @@ def run_gpu(args, rank, world, local_rank):
             "form": best_prec, "value": best_value, "unit": METRIC,
             "speedup_vs_fp64": variants[best_prec]["speedup_vs_fp64"],
             "l2_error_ratio_vs_fp64": variants[best_prec]["l2_error_ratio_vs_fp64"]}
+        variants["delay_modes"] = delay_mode_runs(adg, stream, steps_per, args.variant_steps, dt)
 
     batched = None
     if world == 1 and not args.no_batch:
         batched = batched_run(adg, stream)
     tgv = None
     if world == 1 and not args.no_3d:
-        tgv = tgv_run(adg, stream)
+        tgv = tgv_run(adg, stream, mpk, flush, with_cpu=not args.no_cpu_baseline)
     learned_line = None
     if world == 1 and not args.no_learned:
         learned_line = learned_run(adg, stream)
@@ -587,10 +747,13 @@ def run_gpu(args, rank, world, local_rank):
                     "d2h_bytes_per_step": state_bytes},
             "roofline": roof, "cpu_baseline": cpu,
             "clocks": clocks,
-            "gpu_launches": int(vol_n + flux_n),
-            "kernels": {"vol_kernel": {"ms_per_launch": vol_ms / max(vol_n, 1), "launches": vol_n},
+            "gpu_launches": int(round(launches_per_step * args.steps)),
+            "kernels": {"timing": f"separate profiled pass of {args.profile_steps} benchmark steps "
+                                  "after the timed region (library CUDA events per launch)",
+                        "vol_kernel": {"ms_per_launch": vol_ms / max(vol_n, 1), "launches": vol_n},
                         "flux_kernel": {"ms_per_launch": flux_ms / max(flux_n, 1),
                                         "launches": flux_n}},
+            "measured_peaks_tflops": mpk,
             "variants": variants, "batched": batched, "taylor_green_3d": tgv,
             "learned_ghost": learned_line}
     print(json.dumps(line), flush=True)
@@ -603,7 +766,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "df64"])
-    ap.add_argument("--cpu-steps", type=int, default=4)  # about 12 s of oracle work
+    ap.add_argument("--cpu-steps", type=int, default=4)  # all-cores oracle time steps
+    ap.add_argument("--cpu-steps-single", type=int, default=2)  # about 6 s on one core
+    ap.add_argument("--profile-steps", type=int, default=2,
+                    help="benchmark steps of the profiled pass (per-kernel times)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the FP64 / FP32-pair / FP32 comparison runs")

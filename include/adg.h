@@ -246,10 +246,11 @@ adg_status adg_rhs_noalloc(const adg_mesh* mesh, int degree, double gamma, const
  *   4: packed FP32x2 FMA.
  * tflops receives the best of three timed launches (about 50 ms each at the nominal
  * rates) in TFLOP/s (an FMA counts as 2 flops, an m8n8k4 MMA as 512 per warp); ms
- * (nullable) that launch's duration.  Allocates and frees a small device buffer and a
- * private stream; waits for its own launches.  Errors: ADG_ERR_INVALID, ADG_ERR_CUDA
- * (adg_last_error(NULL) has the text). */
-adg_status adg_measure_peak(int kind, double* tflops, double* ms);
+ * (nullable) that launch's duration; sm_mhz (nullable) the SM clock during it (clock64
+ * cycles of one thread over the global nanosecond timer).  Allocates and frees a small
+ * device buffer and a private stream; waits for its own launches.  Errors:
+ * ADG_ERR_INVALID, ADG_ERR_CUDA (adg_last_error(NULL) has the text). */
+adg_status adg_measure_peak(int kind, double* tflops, double* ms, double* sm_mhz);
 
 /* Message for the last failing call on s (NULL: on this thread, for calls without a
  * handle).  Valid until the next call on the same handle/thread. */

@@ -120,7 +120,7 @@ def lib():
             "adg_host_rk": ([I, P, P, P, P], I),
             "adg_host_schedule": ([I, I, I, I, I, P, U64, I, I64, I, P, P, P], I),
             "adg_host_num_interfaces": ([I, P], I),
-            "adg_measure_peak": ([I, P, P], I),
+            "adg_measure_peak": ([I, P, P, P], I),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -202,10 +202,11 @@ PEAK_KINDS = {"fp64_fma": 0, "fp32_fma": 1, "fp64_mma": 2, "fp64_fma+mma": 3, "f
 
 def measure_peak(kind):
     """Measured arithmetic rate of one instruction kind on the current device:
-    (TFLOP/s, ms of the timed launch).  Kinds: PEAK_KINDS."""
-    t, ms = ctypes.c_double(), ctypes.c_double()
-    _check(lib().adg_measure_peak(PEAK_KINDS[kind], ctypes.byref(t), ctypes.byref(ms)))
-    return t.value, ms.value
+    (TFLOP/s, ms of the timed launch, SM MHz during it).  Kinds: PEAK_KINDS."""
+    t, ms, mhz = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().adg_measure_peak(PEAK_KINDS[kind], ctypes.byref(t), ctypes.byref(ms),
+                                  ctypes.byref(mhz)))
+    return t.value, ms.value, mhz.value
 
 
 def rhs_noalloc(dim, n_elem, degree, u, k, lo=None, hi=None, gamma=1.4, stream=None):

@@ -4,14 +4,16 @@
 // instruction kind and times launches of about 50 ms with CUDA events (best of three, after
 // a warm-up launch).
 //
-//   kind 0  FP64 FMA (DFMA):               8 independent chains per thread
-//   kind 1  FP32 FMA (FFMA):               8 independent chains per thread
+//   kind 0  FP64 FMA (DFMA):               12 independent chains per thread
+//   kind 1  FP32 FMA (FFMA):               12 independent chains per thread
 //   kind 2  FP64 tensor MMA (DMMA):        mma.sync m8n8k4 f64, 4 independent accumulators per warp
 //   kind 3  DFMA and DMMA together:        even warps run kind 0, odd warps kind 2
-//   kind 4  packed FP32x2 FMA (FFMA2):     8 independent chains of float2 per thread
+//   kind 4  packed FP32x2 FMA (FFMA2):     12 independent chains of float2 per thread
 //
 // Kind 3 tells whether the FP64 tensor path adds throughput to the FP64 FMA pipe (its rate
 // is then close to the sum of kinds 0 and 2) or shares it (close to either alone).
+// The SM clock during the launch is measured too (clock64 cycles of one thread against the
+// global nanosecond timer), so a rate can be stated per SM and clock cycle.
 #include <cuda_runtime.h>
 
 #include <string>
@@ -25,7 +27,7 @@ void noalloc_set_error(const char* msg);  // per-thread error text (host.cu)
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kChains = 8;
+constexpr int kChains = 12;
 
 __device__ __forceinline__ void dfma_chains(double (&a)[kChains], double b, double c, int iters) {
   for (int i = 0; i < iters; ++i) {
@@ -47,9 +49,21 @@ __device__ __forceinline__ void dmma_chains(double (&acc)[4][2], double a, doubl
 
 // The results feed a store that never happens for these inputs (|a| stays below 2), so
 // the compiler keeps every operation.
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 __global__ void __launch_bounds__(kThreads) probe_kernel(int kind, int iters, double seed,
-                                                         double* sink) {
+                                                         double* sink, long long* clk) {
   const int warp = threadIdx.x >> 5;
+  long long c0 = 0;
+  unsigned long long t0 = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    c0 = clock64();
+    t0 = global_ns();
+  }
   const bool use_mma = kind == 2 || (kind == 3 && (warp & 1));
   if (kind == 1) {
     float a[kChains];
@@ -97,6 +111,10 @@ __global__ void __launch_bounds__(kThreads) probe_kernel(int kind, int iters, do
     for (int j = 0; j < kChains; ++j) s += a[j];
     if (s > 1e300) sink[blockIdx.x] = s;
   }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    clk[0] = clock64() - c0;
+    clk[1] = (long long)(global_ns() - t0);
+  }
 }
 
 // flops of one launch: per FMA thread 2 * kChains * iters (FP32x2: twice that); per MMA
@@ -121,7 +139,7 @@ adg_status probe_fail(adg_status st, const std::string& m) {
 
 }  // namespace
 
-extern "C" adg_status adg_measure_peak(int kind, double* tflops, double* ms) {
+extern "C" adg_status adg_measure_peak(int kind, double* tflops, double* ms, double* sm_mhz) {
   if (kind < 0 || kind > 4 || !tflops) return probe_fail(ADG_ERR_INVALID, "bad peak-probe arguments");
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -130,24 +148,31 @@ extern "C" adg_status adg_measure_peak(int kind, double* tflops, double* ms) {
   // four blocks of 256 threads per SM: 32 warps per SM, eight per sub-partition
   const int blocks = sms * 4;
   // about 50 ms per launch at the nominal rates (FP64 1.25, FP32 75 TFLOP/s)
-  const int iters = (kind == 1) ? 1500000 : (kind == 4 ? 750000 : 25000);
+  const int iters = (kind == 1) ? 1000000 : (kind == 4 ? 500000 : 16000);
   double* sink = nullptr;
   cudaStream_t s = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&sink, (size_t)blocks * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&sink, (size_t)blocks * sizeof(double) + 16);
+  long long* clk = reinterpret_cast<long long*>(sink + blocks);
   float best = 0.f;
+  double mhz = 0.0;
   for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {  // first launch is a warm-up
     e = cudaEventRecord(e0, s);
-    if (e == cudaSuccess) probe_kernel<<<blocks, kThreads, 0, s>>>(kind, iters, 0.5, sink);
+    if (e == cudaSuccess) probe_kernel<<<blocks, kThreads, 0, s>>>(kind, iters, 0.5, sink, clk);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaEventRecord(e1, s);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
     float t = 0.f;
     if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
-    if (e == cudaSuccess && rep > 0 && (best == 0.f || t < best)) best = t;
+    long long c[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpy(c, clk, sizeof(c), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && rep > 0 && (best == 0.f || t < best)) {
+      best = t;
+      mhz = c[1] > 0 ? 1e3 * (double)c[0] / (double)c[1] : 0.0;
+    }
   }
   if (sink) cudaFree(sink);
   if (e0) cudaEventDestroy(e0);
@@ -156,5 +181,6 @@ extern "C" adg_status adg_measure_peak(int kind, double* tflops, double* ms) {
   if (e != cudaSuccess) return probe_fail(ADG_ERR_CUDA, std::string("peak probe: ") + cudaGetErrorString(e));
   *tflops = launch_flops(kind, blocks, iters) / (best * 1e-3) / 1e12;
   if (ms) *ms = best;
+  if (sm_mhz) *sm_mhz = mhz;
   return ADG_OK;
 }

@@ -28,10 +28,11 @@ def test_peak_probe_rates_are_plausible():
     # GB300 nominal: FP64 1.25 TFLOP/s, FP32 about 75; the probe must land near them and
     # order them (FP32 far above FP64)
     from paper_2603_28710_gb300 import adg
-    f64, ms64 = adg.measure_peak("fp64_fma")
-    f32, _ = adg.measure_peak("fp32_fma")
-    mma, _ = adg.measure_peak("fp64_mma")
-    both, _ = adg.measure_peak("fp64_fma+mma")
+    f64, ms64, mhz = adg.measure_peak("fp64_fma")
+    f32, _, _ = adg.measure_peak("fp32_fma")
+    mma, _, _ = adg.measure_peak("fp64_mma")
+    both, _, _ = adg.measure_peak("fp64_fma+mma")
     assert 0.3 < f64 < 3.0 and ms64 > 5.0
+    assert 500.0 < mhz < 3000.0
     assert 20.0 < f32 < 150.0 and f32 > 10 * f64
     assert mma > 0.0 and both > 0.0
