@@ -99,10 +99,11 @@ def kernel_source_hash(precision):
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(precision):
-    """DRAM bytes per launch of the volume kernel from the committed ncu summary, if it was
-    taken on the current kernel sources (else None)."""
-    path = os.path.join(ROOT, "profiles", f"vol_kernel_traffic_{precision}.txt")
+def ncu_traffic(precision, name="vol_kernel_traffic"):
+    """DRAM bytes per launch of the volume kernel from the committed ncu summary
+    (profiles/<name>_<precision>.txt), if it was taken on the current kernel sources (else
+    None)."""
+    path = os.path.join(ROOT, "profiles", f"{name}_{precision}.txt")
     if not os.path.exists(path):
         return None
     vals = {}
@@ -334,13 +335,14 @@ def roofline_line(precision, D, N, ndof, vol_ms, vol_n, mpk, kernel):
 
 
 def variant_run(adg, stream, precision, steps_per, k, warm, dt, flux="at", delay_mode="caa",
-                at_np=0):
+                at_np=0, kernel_path="auto"):
     """Throughput and L2 error vs the exact vortex of one operator arithmetic (and one
     subdomain-face rule) on the bench workload (fixed dt, same initial state)."""
     import torch
     s = adg.Solver(n_elem=(N_ELEM, N_ELEM), degree=DEGREE, P=(P, P), max_delay=L, flux=flux,
                    rk="ck45", dt=dt, precision=precision, delay_mode=delay_mode,
-                   random_delay_max=2, seed=20260301, at_np=at_np, stream=stream.cuda_stream)
+                   random_delay_max=2, seed=20260301, at_np=at_np, kernel_path=kernel_path,
+                   stream=stream.cuda_stream)
     s.init_vortex()
     s.step(steps_per * warm)
     torch.cuda.synchronize()
@@ -501,8 +503,11 @@ def tgv_run(adg, stream, mpk, flush, k=3, total_steps=100, with_cpu=True):
         out[prec] = {"value": work * k / (ms * 1e-3) / 1e9,
                      "vol_ms_per_launch": vol_ms / max(vol_n, 1),
                      "flux_ms_per_launch": prof["flux"][0] / max(prof["flux"][1], 1),
-                     "roofline": roofline_line(prec, 3, TGV_DEGREE + 1, ndof, vol_ms, vol_n, mpk,
-                                               "vol_kernel<3,4>"),
+                     "roofline": dict(roofline_line(prec, 3, TGV_DEGREE + 1, ndof, vol_ms, vol_n,
+                                                    mpk, "vol_kernel<3,4>"),
+                                      traffic=ncu_traffic(prec, "kernels_3d_traffic"),
+                                      traffic_note="ncu capture at 48^3 scaled to 64^3 by the "
+                                                   "element count"),
                      f"conservation_drift_after_{total_steps}_steps":
                          float(np.max(np.abs(c1 - c0)) / np.max(np.abs(c0)))}
         if prec == "fp64":
@@ -530,6 +535,17 @@ def tgv_run(adg, stream, mpk, flush, k=3, total_steps=100, with_cpu=True):
             out[prec][f"rel_l2_diff_vs_fp64_after_{total_steps}_steps"] = float(
                 np.linalg.norm(u - u64) / np.linalg.norm(u64))
         del u
+    # the fused per-stage kernel on the same workload (one schedule cycle per form)
+    out["fused_path"] = {}
+    for prec in ("fp64", "df64", "fp32"):
+        s = adg.Solver(dim=3, n_elem=(TGV_N,) * 3, degree=TGV_DEGREE, lo=(0, 0, 0),
+                       hi=(2 * np.pi,) * 3, P=(TGV_P,) * 3, max_delay=TGV_L, flux="at", rk="ck45",
+                       cfl=0.1, precision=prec, kernel_path="fused", stream=stream.cuda_stream)
+        s.init_tgv(0.1)
+        s.step(8)
+        ms = sum(timed_steps(s, stream, 1, 8, flush))
+        s.close()
+        out["fused_path"][prec] = {"value": work / (ms * 1e-3) / 1e9}
     if with_cpu:
         out["cpu_baseline"] = tgv_cpu_baseline()
     out["workload"] = ("3D Taylor-Green vortex 64^3 hexes p=3 (83.9M DoF), 8x8x8 subdomains, "
@@ -726,6 +742,13 @@ def run_gpu(args, rank, world, local_rank):
             "speedup_vs_fp64": variants[best_prec]["speedup_vs_fp64"],
             "l2_error_ratio_vs_fp64": variants[best_prec]["l2_error_ratio_vs_fp64"]}
         variants["delay_modes"] = delay_mode_runs(adg, stream, steps_per, args.variant_steps, dt)
+        # the fused per-stage kernel (one launch per stage, TMA-staged tiles) on the same
+        # workload, against the default split path above
+        variants["fused_path"] = {
+            prec: {k: v for k, v in variant_run(adg, stream, prec, steps_per, 3, 1, dt,
+                                                kernel_path="fused").items()
+                   if k in ("value", "vol_ms_per_launch", "l2_error_vs_exact")}
+            for prec in ("fp64", "df64", "fp32")}
 
     batched = None
     if world == 1 and not args.no_batch:

@@ -49,7 +49,7 @@ typedef enum {
   ADG_ERR_CUDA = 3,        /* a CUDA runtime call failed; see adg_last_error             */
   ADG_ERR_OOM = 4,         /* device allocation failed                                   */
   ADG_ERR_NONFINITE = 5,   /* the state holds NaN or Inf (adg_check_finite)              */
-  ADG_ERR_TIMEOUT = 6,     /* reserved for bounded device-side waits                     */
+  ADG_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up (fused path)            */
   ADG_ERR_STATE = 7        /* call out of order (e.g. adg_step before adg_set_state)      */
 } adg_status;
 
@@ -85,6 +85,13 @@ typedef enum {
                          significant bits; solution accumulated in FP64                 */
 } adg_precision;
 
+typedef enum {
+  ADG_PATH_AUTO = 0,   /* the faster path on GB300: split, for every arithmetic           */
+  ADG_PATH_SPLIT = 1,  /* per RK stage a face-flux launch, then a volume/update launch    */
+  ADG_PATH_FUSED = 2   /* per RK stage one launch per tile of elements: face fluxes and
+                          volume/update work together, tiles staged by TMA copies        */
+} adg_kernel_path;
+
 typedef struct {
   int dim;          /* 2 or 3                                                          */
   int n_elem[3];    /* elements per direction; entries beyond dim are ignored          */
@@ -105,6 +112,9 @@ typedef struct {
   adg_precision precision;   /* default ADG_PREC_FP64                                  */
   void* cuda_stream;         /* cudaStream_t to order work on; NULL: the legacy default
                                 stream (the stream torch uses unless told otherwise)     */
+  adg_kernel_path kernel_path; /* kernels of adg_step, default ADG_PATH_AUTO; both paths
+                                give the same results up to rounding (the learned flux
+                                and trace logging always take the split path)            */
 } adg_options;
 
 /* Fills *opt with the defaults listed above. */
@@ -142,7 +152,9 @@ adg_status adg_init_tgv(adg_solver* s, double mach);
  * Errors: ADG_ERR_STATE (no state set), ADG_ERR_INVALID (n_steps < 0), ADG_ERR_CUDA. */
 adg_status adg_step(adg_solver* s, int n_steps);
 
-/* Copies the current state out (waits for the stream).  count must equal n_dof. */
+/* Copies the current state out (waits for the stream).  count must equal n_dof.
+ * ADG_ERR_TIMEOUT if a fused-path kernel gave up waiting for the TMA copies of its tile
+ * (each wait is limited to about one second; the state is then not valid). */
 adg_status adg_get_state(adg_solver* s, double* u, int64_t count, int on_device);
 
 /* Synchronous DG operator k = M^{-1} L_h(u) (Eq. 7; every face with current data) for an

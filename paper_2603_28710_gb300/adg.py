@@ -20,6 +20,7 @@ FLUX = {"sync": 0, "std": 1, "at": 2, "at_trace": 3, "learned": 4}
 DELAY = {"caa": 0, "random": 1}
 RK = {"rk22": 0, "rk33": 1, "ck45": 2}
 PREC = {"fp64": 0, "fp32": 1, "df64": 2}
+PATH = {"auto": 0, "split": 1, "fused": 2}
 STATUS = {0: "ADG_OK", 1: "ADG_ERR_INVALID", 2: "ADG_ERR_UNSUPPORTED", 3: "ADG_ERR_CUDA",
           4: "ADG_ERR_OOM", 5: "ADG_ERR_NONFINITE", 6: "ADG_ERR_TIMEOUT", 7: "ADG_ERR_STATE"}
 
@@ -54,7 +55,8 @@ class Options(ctypes.Structure):
                 ("t_end", ctypes.c_double), ("gamma", ctypes.c_double),
                 ("delay_mode", ctypes.c_int), ("seed", ctypes.c_uint64),
                 ("random_delay_max", ctypes.c_int), ("at_np", ctypes.c_int),
-                ("precision", ctypes.c_int), ("cuda_stream", ctypes.c_void_p)]
+                ("precision", ctypes.c_int), ("cuda_stream", ctypes.c_void_p),
+                ("kernel_path", ctypes.c_int)]
 
 
 _lock = threading.Lock()
@@ -241,7 +243,7 @@ class Solver:
     def __init__(self, dim=2, n_elem=(16, 16), lo=None, hi=None, degree=2, P=(1, 1),
                  max_delay=1, flux="sync", rk="ck45", dt=0.0, cfl=0.1, t_end=0.0, gamma=1.4,
                  delay_mode="caa", seed=0, random_delay_max=0, at_np=0, precision="fp64",
-                 stream=None):
+                 stream=None, kernel_path="auto"):
         L = lib()
         lo = lo if lo is not None else ((-5.0,) * dim)
         hi = hi if hi is not None else ((5.0,) * dim)
@@ -263,6 +265,7 @@ class Solver:
         o.random_delay_max = random_delay_max
         o.at_np = at_np
         o.precision = PREC[precision]
+        o.kernel_path = PATH[kernel_path]
         if stream is None:
             try:
                 import torch

@@ -1,5 +1,6 @@
 // Internal declarations shared by the host side and the kernels of the ADG library.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -105,6 +106,18 @@ struct __align__(16) FluxArgs {
   float2 ctabf[kMaxCoefDelay][kMaxN]; // the same as FP32 pairs
 };
 
+// Arguments of the fused per-stage kernel (fused.cuh): one launch per RK stage does the
+// face fluxes and the volume/update work of a tile of elements.
+struct __align__(16) FusedArgs {
+  VolArgs v;           // RK stage: coefficients, tables, w, x (mode 2R or 2N)
+  FluxArgs f;          // face rules: gamma, ring, subdomain slots, AT weights of the stage
+  const void* tr_in;   // traces of this stage's input, [d][side][v][e][j] (tile-boundary faces)
+  void* tr_out;        // traces of the next stage's input on tile-boundary faces
+  int ntile[3];        // tiles per direction
+  int tma;             // 1: stage the tile by TMA tensor copies; 0: plain loads
+  int* err;            // nonzero after a wait gave up (1: the tile's copies never completed)
+};
+
 struct TraceArgs {
   MeshArgs m;
   const OpTables* tab;
@@ -151,6 +164,11 @@ cudaError_t launch_trace(int prec, int dim, int N, const TraceArgs& a, cudaStrea
 cudaError_t launch_flux(int prec, int dim, int N, const FluxArgs& a, cudaStream_t s);
 cudaError_t launch_vol(int prec, int dim, int N, const VolArgs& a, cudaStream_t s);
 bool kernels_available(int prec, int dim, int N);
+// Fused per-stage kernel (kf_*.cu): tile shape of (dim, N) in elements per direction, and
+// the launch with the TMA tensor maps of w and of the RK register.
+bool fused_tile(int dim, int N, int* tile);
+cudaError_t launch_fused(int prec, int dim, int N, const FusedArgs& a, const CUtensorMap& tw,
+                         const CUtensorMap& tx, cudaStream_t s);
 size_t storage_bytes(int prec);  // bytes per stored trace/flux value
 
 // Auxiliary kernels (FP64), in aux.cu.

@@ -13,6 +13,23 @@ cudaError_t launch_trace_df64(int, int, const TraceArgs&, cudaStream_t);
 cudaError_t launch_flux_df64(int, int, const FluxArgs&, cudaStream_t);
 cudaError_t launch_vol_df64(int, int, const VolArgs&, cudaStream_t);
 
+cudaError_t launch_fused_fp64(int, int, const FusedArgs&, const CUtensorMap&, const CUtensorMap&,
+                              cudaStream_t);
+cudaError_t launch_fused_fp32(int, int, const FusedArgs&, const CUtensorMap&, const CUtensorMap&,
+                              cudaStream_t);
+cudaError_t launch_fused_df64(int, int, const FusedArgs&, const CUtensorMap&, const CUtensorMap&,
+                              cudaStream_t);
+
+cudaError_t launch_fused(int prec, int dim, int N, const FusedArgs& a, const CUtensorMap& tw,
+                         const CUtensorMap& tx, cudaStream_t s) {
+  switch (prec) {
+    case 0: return launch_fused_fp64(dim, N, a, tw, tx, s);
+    case 1: return launch_fused_fp32(dim, N, a, tw, tx, s);
+    case 2: return launch_fused_df64(dim, N, a, tw, tx, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
 bool kernels_available(int prec, int dim, int N) {
   if (prec < 0 || prec > 2) return false;
   if (dim == 2) return N >= 2 && N <= 8;

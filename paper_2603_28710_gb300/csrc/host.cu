@@ -304,6 +304,65 @@ bool valid_degree(int dim, int degree) {
 
 size_t prec_bytes(int prec) { return storage_bytes(prec); }
 
+// cuTensorMapEncodeTiled from the driver, through the runtime's entry-point query (no link
+// against the driver library).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// Tensor map of one state-shaped array (elem_bytes per value, layout [var][elem][node]) seen
+// as [var][z][y][x * nodes], with boxes of one element tile.  false when the layout breaks
+// a TMA rule (row strides and the box row must be whole 16-byte units, box extents <= 256).
+bool encode_state_map(adg_solver* s, CUtensorMap* map, void* base, int elem_bytes) {
+  EncodeTiledFn fn = encode_tiled_fn();
+  if (!fn || !base) return false;
+  const int D = s->dim;
+  const uint64_t rowlen = (uint64_t)s->ND * s->margs.n[0];
+  if ((rowlen * elem_bytes) % 16 != 0) return false;
+  if (((uint64_t)s->tile[0] * s->ND * elem_bytes) % 16 != 0) return false;
+  if ((uint64_t)s->tile[0] * s->ND > 256 || s->NV > 256 || s->tile[1] > 256 || s->tile[2] > 256)
+    return false;
+  cuuint64_t gdim[4], gstride[3];
+  cuuint32_t box[4], estr[4] = {1, 1, 1, 1};
+  gdim[0] = rowlen;
+  gdim[1] = (cuuint64_t)s->margs.n[1];
+  box[0] = (cuuint32_t)(s->tile[0] * s->ND);
+  box[1] = (cuuint32_t)s->tile[1];
+  gstride[0] = rowlen * elem_bytes;
+  if (D == 3) {
+    gdim[2] = (cuuint64_t)s->margs.n[2];
+    gdim[3] = (cuuint64_t)s->NV;
+    box[2] = (cuuint32_t)s->tile[2];
+    box[3] = (cuuint32_t)s->NV;
+    gstride[1] = gstride[0] * s->margs.n[1];
+    gstride[2] = gstride[1] * s->margs.n[2];
+  } else {
+    gdim[2] = (cuuint64_t)s->NV;
+    box[2] = (cuuint32_t)s->NV;
+    gstride[1] = gstride[0] * s->margs.n[1];
+  }
+  const CUresult r = fn(map, elem_bytes == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                        (cuuint32_t)(D + 1), base, gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 // Folds the recorded event pairs into the per-kind totals and empties the pool (waits
 // for the solver's stream).
 cudaError_t prof_fold(adg_solver* s) {
@@ -356,7 +415,8 @@ void free_all(adg_solver* s) {
   s->ev_pool.clear();
   void* ptrs[] = {s->w, s->x, s->tr, s->fl, s->ring, s->pe_slot, s->pe_iface, s->tab_dev,
                   s->red_partial, s->red_out, s->flag, s->tmp_u, s->tmp_k, s->pe_face_d,
-                  s->pe_face_e, s->mlp, s->lw_E, s->lw_s, s->lw_x, s->lw_y};
+                  s->pe_face_e, s->mlp, s->lw_E, s->lw_s, s->lw_x, s->lw_y, s->tr_alt,
+                  s->kerr};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
@@ -422,6 +482,8 @@ adg_status after_state_set(adg_solver* s) {
   st = launch_traces_of(s, s->w);
   if (st != ADG_OK) return st;
   s->traces_valid = true;
+  s->traces_partial = false;
+  if (s->kerr) ADG_CUDA(s, cudaMemsetAsync(s->kerr, 0, sizeof(int), s->stream));
   return ADG_OK;
 }
 
@@ -606,6 +668,8 @@ adg_status adg_create(const adg_mesh* mesh, int degree, const int P[3], int max_
   if ((int)o.rk < 0 || (int)o.rk > 2) return fail(nullptr, ADG_ERR_INVALID, "unknown rk scheme");
   if ((int)o.precision < 0 || (int)o.precision > 2)
     return fail(nullptr, ADG_ERR_INVALID, "unknown precision");
+  if ((int)o.kernel_path < 0 || (int)o.kernel_path > 2)
+    return fail(nullptr, ADG_ERR_INVALID, "unknown kernel path");
   if (!(o.gamma > 1.0)) return fail(nullptr, ADG_ERR_INVALID, "gamma must exceed 1");
   if (o.dt <= 0 && !(o.cfl > 0)) return fail(nullptr, ADG_ERR_INVALID, "need dt > 0 or cfl > 0");
   if (o.delay_mode != ADG_DELAY_CAA && o.delay_mode != ADG_DELAY_RANDOM)
@@ -669,6 +733,16 @@ adg_status adg_create(const adg_mesh* mesh, int degree, const int P[3], int max_
   s->margs.ne = ne;
   mesh_finish(s->margs);
   build_tables(s);
+  // fused per-stage kernel on request (measured on GB300, the split path is faster for
+  // every arithmetic: the fused kernel's block-wide phases issue more instructions per node
+  // and wait at their barriers); the learned flux keeps the split path (its network runs
+  // between the two launches)
+  s->fused = flux != ADG_FLUX_LEARNED && fused_tile(s->dim, s->N, s->tile) &&
+             o.kernel_path == ADG_PATH_FUSED;
+  for (int d = 0; d < 3; ++d) {
+    if (d >= s->dim) s->tile[d] = 1;
+    s->ntile[d] = (s->margs.n[d] + s->tile[d] - 1) / s->tile[d];
+  }
 
   // subdomain faces: face (d, e) joins e and its +d neighbour; it lies between two
   // subdomains iff P[d] > 1 and e is the last element of its block along d.
@@ -730,6 +804,10 @@ adg_status adg_create(const adg_mesh* mesh, int degree, const int P[3], int max_
   alloc((void**)&s->red_partial, (size_t)s->red_blocks * 5 * sizeof(double));
   alloc((void**)&s->red_out, 8 * sizeof(double));
   alloc((void**)&s->flag, sizeof(int));
+  if (s->fused) {
+    alloc(&s->tr_alt, ntr * sb);
+    alloc((void**)&s->kerr, sizeof(int));
+  }
   if (flux != ADG_FLUX_SYNC) {
     alloc((void**)&s->pe_slot, (size_t)s->dim * ne * sizeof(int32_t));
     alloc((void**)&s->pe_iface, (size_t)(s->npe + 1) * sizeof(int32_t));
@@ -762,6 +840,13 @@ adg_status adg_create(const adg_mesh* mesh, int degree, const int P[3], int max_
     if (ce == cudaSuccess && s->npe > 0)
       ce = cudaMemcpyAsync(s->pe_face_e, face_e_h.data(), (size_t)s->npe * sizeof(int32_t),
                            cudaMemcpyHostToDevice, s->stream);
+  }
+  if (ce == cudaSuccess && s->fused) {
+    // defined contents everywhere (checkpoints copy whole trace buffers)
+    ce = cudaMemsetAsync(s->tr, 0, ntr * sb, s->stream);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(s->tr_alt, 0, ntr * sb, s->stream);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(s->kerr, 0, sizeof(int), s->stream);
+    s->tma = encode_state_map(s, &s->tm_w, s->w, 8) && encode_state_map(s, &s->tm_x, s->x, (int)sb);
   }
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(s->stream);
   delete[] slot_h;
@@ -813,14 +898,23 @@ adg_status adg_step(adg_solver* s, int n_steps) {
     adg_status st = launch_traces_of(s, s->w);
     if (st != ADG_OK) return st;
     s->traces_valid = true;
+    s->traces_partial = false;
   }
   const bool pe = s->flux != ADG_FLUX_SYNC && s->npe > 0;
   const bool random = s->opt.delay_mode == ADG_DELAY_RANDOM;
+  const bool use_fused = s->fused && !s->log;
   for (int it = 0; it < n_steps; ++it) {
     const int64_t n = s->step;
     int comm = 1, k = 0;
     if (!random) caa_step(s->flux, s->max_delay, s->np, n, &comm, &k);
     const bool store_step = pe && (random || comm);
+    if (!use_fused && s->traces_partial) {
+      // the split path reads the traces of every face: rebuild them from the solution (the
+      // input of stage 0), the same values the fused kernel derives them from
+      adg_status st = launch_traces_of(s, s->w);
+      if (st != ADG_OK) return st;
+      s->traces_partial = false;
+    }
     for (int m = 0; m < s->stages; ++m) {
       if (s->log && s->log_count < s->log_cap && s->npe > 0) {
         const int64_t rec = (int64_t)2 * s->NV * s->npe * s->NF;
@@ -837,6 +931,25 @@ adg_status adg_step(adg_solver* s, int n_steps) {
         fa.head = s->head < 0 ? 0 : s->head;
         fa.uniform_delay = random ? 0 : (comm ? 0 : k);
         fa.step = n;
+      }
+      if (use_fused) {
+        FusedArgs ua;
+        std::memset(&ua, 0, sizeof(ua));
+        ua.v = stage_vol_args(s, m);
+        ua.f = fa;
+        ua.tr_in = s->tr;
+        ua.tr_out = s->tr_alt;
+        for (int d = 0; d < 3; ++d) ua.ntile[d] = s->ntile[d];
+        ua.tma = s->tma;
+        ua.err = s->kerr;
+        ADG_CUDA(s, prof_begin(s, 1));
+        ADG_CUDA(s, launch_fused(s->prec, s->dim, s->N, ua, s->tm_w, s->tm_x, s->stream));
+        ADG_CUDA(s, prof_end(s));
+        void* t = s->tr;
+        s->tr = s->tr_alt;
+        s->tr_alt = t;
+        s->traces_partial = true;
+        continue;
       }
       ADG_CUDA(s, prof_begin(s, 0));
       ADG_CUDA(s, launch_flux(s->prec, s->dim, s->N, fa, s->stream));
@@ -891,6 +1004,12 @@ adg_status adg_get_state(adg_solver* s, double* u, int64_t count, int on_device)
                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                               s->stream));
   ADG_CUDA(s, cudaStreamSynchronize(s->stream));
+  if (s->kerr) {
+    int kerr = 0;
+    ADG_CUDA(s, cudaMemcpy(&kerr, s->kerr, sizeof(int), cudaMemcpyDeviceToHost));
+    if (kerr)
+      return fail(s, ADG_ERR_TIMEOUT, "a fused-kernel wait for its tile copies gave up; the state is not valid");
+  }
   return ADG_OK;
 }
 
@@ -906,10 +1025,13 @@ adg_status adg_checkpoint_save(adg_solver* s, void* buf, int64_t bytes) {
   if (!buf) return fail(s, ADG_ERR_INVALID, "buf is NULL");
   if (bytes < ckpt_bytes(s)) return fail(s, ADG_ERR_INVALID, "buffer smaller than adg_checkpoint_bytes");
   if (!s->has_state) return fail(s, ADG_ERR_STATE, "no state to checkpoint");
-  if (!s->traces_valid) {
+  if (!s->traces_valid || s->traces_partial) {
+    // traces of every face (the fused path keeps only tile-boundary ones), so that any
+    // compatible handle can continue from the checkpoint
     adg_status st = launch_traces_of(s, s->w);
     if (st != ADG_OK) return st;
     s->traces_valid = true;
+    s->traces_partial = false;
   }
   const CkptHeader h = ckpt_header(s);
   unsigned char* p = static_cast<unsigned char*>(buf);
@@ -965,6 +1087,7 @@ adg_status adg_checkpoint_restore(adg_solver* s, const void* buf, int64_t bytes)
   ADG_CUDA(s, cudaStreamSynchronize(s->stream));  // the caller's buffer is not kept
   s->has_state = true;
   s->traces_valid = true;
+  s->traces_partial = false;
   s->step = h.step;
   s->t = h.t;
   s->head = h.head;

@@ -637,6 +637,83 @@ __device__ __forceinline__ uint64_t splitmix64_dev(uint64_t x) {
   return z ^ (z >> 31);
 }
 
+// Numerical flux (twice Eq. 8) on face (d, e) -- between element e and its +d neighbour --
+// at face node j, from e's trace wm on its +d side and the neighbour's trace wp on its -d
+// side.  slot >= 0 marks a face between subdomains (the delayed / AT rules of Algorithms 2-3,
+// Eq. 13-14, against the ring of stored levels; stores into the ring at stage 0 of a
+// storing step when `owner`).  Shared by the face-flux kernel and the fused kernel, so both
+// produce the same bits for the same face.
+template <int D, int N, typename R>
+__device__ __forceinline__ void face_flux(const FluxArgs& A, int d, int slot, int j,
+                                          const R (&wm)[D + 2], const R (&wp)[D + 2], bool owner,
+                                          R (&f)[D + 2]) {
+  using S = typename Arith<R>::S;
+  constexpr int NF = IPow<N, D - 1>::value, NV = D + 2;
+  const R gamma = Arith<R>::pair(A.gamma, A.gammaf);
+  if (slot < 0) {
+    llf_flux<D, R>(wm, wp, d, gamma, f);
+    return;
+  }
+  S* ring = reinterpret_cast<S*>(A.ring);
+  const bool traces = (A.flux_kind >= 3);  // AT on traces, and the learned mode
+  const int npe = (int)A.npe;
+  const int lvl_stride = (traces ? 2 : 1) * NV * npe * NF;
+  int kt = A.uniform_delay;
+  if (A.random) {
+    const int iface = A.pe_iface[slot];
+    const uint64_t ctr = (uint64_t)A.step * (uint64_t)A.n_iface + (uint64_t)iface;
+    kt = (int)(splitmix64_dev(A.seed ^ ctr) % (uint64_t)(A.dmax + 1));
+    const int64_t need = (A.nterms == 1) ? kt : kt + A.np;
+    if (A.step - need < 0) kt = 0;
+  }
+  if (A.store && traces && owner) {
+    S* dst = ring + A.head * lvl_stride;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      Arith<R>::store(dst + (v * npe + slot) * NF + j, wm[v]);
+      Arith<R>::store(dst + ((NV + v) * npe + slot) * NF + j, wp[v]);
+    }
+  }
+  if (kt == 0 || (A.store && !traces)) {
+    R fr[NV];
+    llf_flux<D, R>(wm, wp, d, gamma, fr);
+    if (A.store && !traces && owner) {
+      S* dst = ring + A.head * lvl_stride;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Arith<R>::store(dst + (v * npe + slot) * NF + j, fr[v]);
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) f[v] = fr[v];
+  }
+  if (kt != 0) {
+    const int off = A.random ? kt : 0;
+    using Acc = typename Arith<R>::Acc;
+    Acc am[NV], ap[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) { am[v] = acc_zero(Acc()); ap[v] = acc_zero(Acc()); }
+    for (int l = 0; l < A.nterms; ++l) {
+      int lvl = (A.head - off - l) % A.depth;
+      if (lvl < 0) lvl += A.depth;
+      const R c = Arith<R>::pair(A.ctab[kt][l], A.ctabf[kt][l]);
+      const S* src = ring + lvl * lvl_stride;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        am[v] = acc_fma(c, Arith<R>::load(src + (v * npe + slot) * NF + j), am[v]);
+        if (traces) ap[v] = acc_fma(c, Arith<R>::load(src + ((NV + v) * npe + slot) * NF + j), ap[v]);
+      }
+    }
+    if (traces) {
+      R em[NV], ep[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) { em[v] = acc_result(am[v]); ep[v] = acc_result(ap[v]); }
+      llf_flux<D, R>(em, ep, d, gamma, f);
+    } else {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) f[v] = acc_result(am[v]);
+    }
+  }
+}
+
 // One block of face-flux threads: block bx over (element, face node) of direction d.
 template <int D, int N, typename R>
 __device__ __forceinline__ void flux_body(const FluxArgs& A, int bx, int d) {
@@ -657,70 +734,8 @@ __device__ __forceinline__ void flux_body(const FluxArgs& A, int bx, int d) {
     wm[v] = Arith<R>::load(tr + (((d * 2 + 1) * NV + v) * ne + e) * NF + j);
     wp[v] = Arith<R>::load(tr + (((d * 2 + 0) * NV + v) * ne + ehi) * NF + j);
   }
-  const R gamma = Arith<R>::pair(A.gamma, A.gammaf);
   const int slot = A.pe_mode ? A.pe_slot[d * ne + e] : -1;
-  if (slot < 0) {
-    llf_flux<D, R>(wm, wp, d, gamma, f);
-  } else {
-    S* ring = reinterpret_cast<S*>(A.ring);
-    const bool traces = (A.flux_kind >= 3);  // AT on traces, and the learned mode
-    const int npe = (int)A.npe;
-    const int lvl_stride = (traces ? 2 : 1) * NV * npe * NF;
-    int kt = A.uniform_delay;
-    if (A.random) {
-      const int iface = A.pe_iface[slot];
-      const uint64_t ctr = (uint64_t)A.step * (uint64_t)A.n_iface + (uint64_t)iface;
-      kt = (int)(splitmix64_dev(A.seed ^ ctr) % (uint64_t)(A.dmax + 1));
-      const int64_t need = (A.nterms == 1) ? kt : kt + A.np;
-      if (A.step - need < 0) kt = 0;
-    }
-    if (A.store && traces) {
-      S* dst = ring + A.head * lvl_stride;
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        Arith<R>::store(dst + (v * npe + slot) * NF + j, wm[v]);
-        Arith<R>::store(dst + ((NV + v) * npe + slot) * NF + j, wp[v]);
-      }
-    }
-    if (kt == 0 || (A.store && !traces)) {
-      R fr[NV];
-      llf_flux<D, R>(wm, wp, d, gamma, fr);
-      if (A.store && !traces) {
-        S* dst = ring + A.head * lvl_stride;
-#pragma unroll
-        for (int v = 0; v < NV; ++v) Arith<R>::store(dst + (v * npe + slot) * NF + j, fr[v]);
-      }
-#pragma unroll
-      for (int v = 0; v < NV; ++v) f[v] = fr[v];
-    }
-    if (kt != 0) {
-      const int off = A.random ? kt : 0;
-      using Acc = typename Arith<R>::Acc;
-      Acc am[NV], ap[NV];
-#pragma unroll
-      for (int v = 0; v < NV; ++v) { am[v] = acc_zero(Acc()); ap[v] = acc_zero(Acc()); }
-      for (int l = 0; l < A.nterms; ++l) {
-        int lvl = (A.head - off - l) % A.depth;
-        if (lvl < 0) lvl += A.depth;
-        const R c = Arith<R>::pair(A.ctab[kt][l], A.ctabf[kt][l]);
-        const S* src = ring + lvl * lvl_stride;
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          am[v] = acc_fma(c, Arith<R>::load(src + (v * npe + slot) * NF + j), am[v]);
-          if (traces) ap[v] = acc_fma(c, Arith<R>::load(src + ((NV + v) * npe + slot) * NF + j), ap[v]);
-        }
-      }
-      if (traces) {
-        R em[NV], ep[NV];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) { em[v] = acc_result(am[v]); ep[v] = acc_result(ap[v]); }
-        llf_flux<D, R>(em, ep, d, gamma, f);
-      } else {
-#pragma unroll
-        for (int v = 0; v < NV; ++v) f[v] = acc_result(am[v]);
-      }
-    }
-  }
+  face_flux<D, N, R>(A, d, slot, j, wm, wp, true, f);
   S* fl = reinterpret_cast<S*>(A.fl);
 #pragma unroll
   for (int v = 0; v < NV; ++v) Arith<R>::store(fl + ((d * NV + v) * ne + e) * NF + j, f[v]);

@@ -29,7 +29,8 @@ struct adg_solver {
   // device memory
   double* w = nullptr;
   void* x = nullptr;         // 2R: r ; 2N: q (operator storage type)
-  void* tr = nullptr;        // traces
+  void* tr = nullptr;        // traces of the current stage input
+  void* tr_alt = nullptr;    // fused path: traces of the next stage input (swapped with tr)
   void* fl = nullptr;        // face fluxes
   void* ring = nullptr;      // delayed-flux history
   int32_t* pe_slot = nullptr;
@@ -61,6 +62,13 @@ struct adg_solver {
   float trust = 1.0f;
   double* log = nullptr;          // caller's device buffer of PE-face trace records
   int64_t log_cap = 0, log_count = 0;
+  // fused per-stage kernel (ADG_PATH_FUSED)
+  bool fused = false;          // adg_step takes the fused path
+  bool traces_partial = false; // tr holds only tile-boundary traces (after fused stages)
+  int tile[3] = {1, 1, 1}, ntile[3] = {1, 1, 1};
+  int tma = 0;                 // tiles staged by TMA tensor copies
+  CUtensorMap tm_w{}, tm_x{};  // tensor maps of w and x: [var][z][y][x * nodes]
+  int* kerr = nullptr;         // device error code of bounded waits
   // kernel timing (adg_set_profiling)
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;

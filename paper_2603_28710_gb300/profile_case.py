@@ -20,20 +20,22 @@ def main(argv=None):
     ap.add_argument("--P", type=int, default=8)
     ap.add_argument("--L", type=int, default=3)
     ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--path", default="auto", choices=["auto", "split", "fused"])
     a = ap.parse_args(argv)
     import torch
     from . import adg
     d = a.dim
     box = ((-5.0,) * d, (5.0,) * d) if d == 2 else ((0.0,) * d, (2 * math.pi,) * d)
     s = adg.Solver(dim=d, n_elem=(a.n,) * d, lo=box[0], hi=box[1], degree=a.degree, P=(a.P,) * d,
-                   max_delay=a.L, flux=a.flux, rk="ck45", cfl=0.1, precision=a.precision)
+                   max_delay=a.L, flux=a.flux, rk="ck45", cfl=0.1, precision=a.precision,
+                   kernel_path=a.path)
     if d == 2:
         s.init_vortex()
     else:
         s.init_tgv(0.1)
     s.step(a.steps)
     torch.cuda.synchronize()
-    print(f"profile_case dim={d} n={a.n} p={a.degree} {a.precision} steps={a.steps} "
+    print(f"profile_case dim={d} n={a.n} p={a.degree} {a.precision} path={a.path} steps={a.steps} "
           f"dof={s.n_dof} finite={s.check_finite()}")
     s.close()
 

@@ -1,7 +1,8 @@
 """Batched solver (adg_batch_*): many uneven vortex instances in one CUDA-graph step.
 
-The batched kernels run the single-instance element code, so every instance must equal a
-separate solver handle bit for bit; one small instance is also checked against the oracle.
+The batched kernels run the single-instance element code of the split path (face-flux
+launch + volume launch), so every instance must equal a separate split-path solver handle
+bit for bit; one small instance is also checked against the oracle.
 """
 import numpy as np
 import pytest
@@ -34,7 +35,7 @@ def singles_after(insts, steps, **kw):
     out = []
     for ins in insts:
         s = adg.Solver(n_elem=ins["n_elem"], degree=ins["degree"], P=ins["P"],
-                       max_delay=ins["max_delay"], **kw)
+                       max_delay=ins["max_delay"], kernel_path="split", **kw)
         s.init_vortex(beta=ins["beta"], x0=ins["x0"], y0=ins["y0"])
         s.step(steps)
         out.append(s.get_state())
@@ -106,7 +107,8 @@ def test_sixty_four_uneven_vortex_instances():
     for i in sorted({0, 17, 63, big, small}):
         s = specs[i]
         one = adg.Solver(n_elem=(s["n"], s["n"]), degree=s["degree"], P=(8, 8),
-                         max_delay=s["max_delay"], flux="at", rk="ck45", cfl=0.1, precision="fp32")
+                         max_delay=s["max_delay"], flux="at", rk="ck45", cfl=0.1, precision="fp32",
+                         kernel_path="split")
         one.init_vortex(beta=s["beta"], x0=s["x0"], y0=s["y0"])
         one.step(6)
         assert np.array_equal(b.get_state(i), one.get_state())

@@ -38,8 +38,12 @@ def summand_scale(u_el, dim, degree, h, gamma=1.4):
 
 
 def elementwise_ok(kg, ko, S):
-    """|kg - ko| <= 1e-12 max|ko| + 64 eps S at every node (kg, ko: [elem][var][node])."""
-    bound = 1e-12 * np.abs(ko).max() + 64 * 2.0 ** -53 * S[:, :, None]
+    """|kg - ko| <= 1e-12 max|ko| + 256 eps S at every node (kg, ko: [elem][var][node]).
+    256: each side's node value sums about 2d (p+1) + 2d products of this size, each side
+    rounds them in its own order, and the face terms carry the rounding of the traces they
+    are evaluated from (measured on GB300: up to about 120 eps S on the 3D Taylor-Green
+    vortex)."""
+    bound = 1e-12 * np.abs(ko).max() + 256 * 2.0 ** -53 * S[:, :, None]
     excess = (np.abs(kg - ko) / bound).max()
     return excess <= 1.0, excess
 
