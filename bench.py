@@ -427,8 +427,50 @@ def batched_run(adg, stream, k=6):
     ms_seq = e0.elapsed_time(e1)
     for s in singles:
         s.close()
+    # the same comparison per mesh size class (the instances of one mesh size as a batch of
+    # their own against their separate handles)
+    by_mesh = {}
+    for nm in sorted({q["n"] for q in specs}):
+        sub = [q for q in specs if q["n"] == nm]
+        wk = sum(4 * q["n"] ** 2 * (q["degree"] + 1) ** 2 for q in sub) * 5
+        bb = adg.Batch([dict(n_elem=(q["n"], q["n"]), degree=q["degree"], P=(8, 8),
+                             max_delay=q["max_delay"]) for q in sub],
+                       flux="at", rk="ck45", cfl=0.1, precision="fp32", stream=stream.cuda_stream)
+        bb.autotune(trials=3)
+        for i, q in enumerate(sub):
+            bb.init_vortex(i, beta=q["beta"], x0=q["x0"], y0=q["y0"])
+        bb.step(2)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        bb.step(k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        mb = e0.elapsed_time(e1)
+        bb.close()
+        ss = []
+        for q in sub:
+            s1 = adg.Solver(n_elem=(q["n"], q["n"]), degree=q["degree"], P=(8, 8),
+                            max_delay=q["max_delay"], flux="at", rk="ck45", cfl=0.1,
+                            precision="fp32", stream=stream.cuda_stream)
+            s1.init_vortex(beta=q["beta"], x0=q["x0"], y0=q["y0"])
+            s1.step(2)
+            ss.append(s1)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(k):
+            for s1 in ss:
+                s1.step(1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        msq = e0.elapsed_time(e1)
+        for s1 in ss:
+            s1.close()
+        by_mesh[f"{nm}^2"] = {"instances": len(sub), "value": wk * k / (mb * 1e-3) / 1e9,
+                              "sequential_handles_value": wk * k / (msq * 1e-3) / 1e9,
+                              "speedup_vs_sequential": msq / mb}
     return {"workload": "64 vortex instances, meshes 32^2..256^2, p 2..5, L 2..4, 8x8 subdomains, "
                         "AT flux, CK4(5), FP32 operator / FP64 accumulation, one CUDA graph per step",
+            "by_mesh": by_mesh,
             "value": work * k / (ms_batch * 1e-3) / 1e9, "unit": METRIC, "steps": k,
             "ms_per_step": ms_batch / k, "sequential_handles_value": work * k / (ms_seq * 1e-3) / 1e9,
             "speedup_vs_sequential": ms_seq / ms_batch, "tile_threads_per_degree_group": tiles,

@@ -116,6 +116,8 @@ struct adg_batch {
     int vtotal = 0, ftotal = 0;
     int vgrid = 0, fgrid = 0;
     int vpersist = 1, fpersist = 1;  // one resident wave looping over tiles, or a block per tile
+    int solo_waves = 4;  // instances filling the GPU this many times get a volume launch of
+                         // their own (0: none do)
   };
   std::vector<Group> groups;
   cudaGraphExec_t exec = nullptr;
@@ -171,11 +173,11 @@ int persistent_grid(int total, int per_sm) {
   return std::max(1, std::min(total, sms * per_sm));
 }
 
-// An instance whose volume tiles fill the GPU this many times over gets a volume launch of
-// its own (arguments in the kernel's parameter bank) instead of a share of the persistent
+// An instance whose volume tiles fill the GPU solo_waves times over (default 4; the
+// autotuner also tries 1 and never) gets a volume launch of its own -- the single-handle
+// kernel, arguments in the kernel's parameter bank -- instead of a share of the persistent
 // launch: a persistent block reads its instance's arguments from shared memory, which costs
 // registers and hence occupancy, while small instances gain more from sharing one launch.
-constexpr int kSoloWaves = 4;
 
 // Split of a group into batched and solo volume work, and virtual-block offsets, for the
 // chosen tile and launch shapes.
@@ -192,7 +194,7 @@ adg_status layout_group(adg_batch* b, adg_batch::Group& g) {
   g.solo.clear();
   for (int i : g.inst) {
     const int64_t tiles = (b->inst[i]->ne + epb - 1) / epb;
-    (tiles >= kSoloWaves * wave ? g.solo : g.vinst).push_back(i);
+    (g.solo_waves > 0 && tiles >= g.solo_waves * wave ? g.solo : g.vinst).push_back(i);
   }
   std::vector<int> voff(g.vinst.size() + 1), foff(g.inst.size() + 1);
   voff[0] = foff[0] = 0;
@@ -455,23 +457,29 @@ adg_status adg_batch_autotune(adg_batch* b, int trials, int* tile_threads) {
   for (size_t gi = 0; gi < b->groups.size(); ++gi) {
     auto& g = b->groups[gi];
     float best = 1e30f, ms = 0.f;
-    int best_tt = 128, best_vp = 1, best_fp = 1;
-    // volume kernel: tile size x launch shape
+    int best_tt = 128, best_vp = 1, best_fp = 1, best_sw = 4;
+    // volume kernel: tile size x launch shape x which instances run the single-handle
+    // launch (those filling the GPU 1 or 4 times over, or none)
+    const int solo_cand[3] = {4, 1, 0};
     for (int tt : cand)
-      for (int vp = 1; vp >= 0; --vp) {
-        g.tt = tt;
-        g.vpersist = vp;
-        adg_status st = layout_group(b, g);
-        if (st == ADG_OK) st = time_group(g, true, &ms);
-        if (st != ADG_OK) return st;
-        if (ms < best) {
-          best = ms;
-          best_tt = tt;
-          best_vp = vp;
+      for (int vp = 1; vp >= 0; --vp)
+        for (int sw : solo_cand) {
+          g.tt = tt;
+          g.vpersist = vp;
+          g.solo_waves = sw;
+          adg_status st = layout_group(b, g);
+          if (st == ADG_OK) st = time_group(g, true, &ms);
+          if (st != ADG_OK) return st;
+          if (ms < best) {
+            best = ms;
+            best_tt = tt;
+            best_vp = vp;
+            best_sw = sw;
+          }
         }
-      }
     g.tt = best_tt;
     g.vpersist = best_vp;
+    g.solo_waves = best_sw;
     // face-flux kernel: launch shape
     best = 1e30f;
     for (int fp = 1; fp >= 0; --fp) {

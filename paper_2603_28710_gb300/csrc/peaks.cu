@@ -30,6 +30,7 @@ constexpr int kThreads = 256;
 constexpr int kChains = 12;
 
 __device__ __forceinline__ void dfma_chains(double (&a)[kChains], double b, double c, int iters) {
+#pragma unroll 4
   for (int i = 0; i < iters; ++i) {
 #pragma unroll
     for (int j = 0; j < kChains; ++j) a[j] = fma(a[j], b, c);
@@ -70,6 +71,7 @@ __global__ void __launch_bounds__(kThreads) probe_kernel(int kind, int iters, do
 #pragma unroll
     for (int j = 0; j < kChains; ++j) a[j] = (float)seed * (j + 1) + threadIdx.x * 1e-7f;
     const float b = 0.999999f, c = 1e-7f;
+#pragma unroll 4
     for (int i = 0; i < iters; ++i) {
 #pragma unroll
       for (int j = 0; j < kChains; ++j) a[j] = fmaf(a[j], b, c);
@@ -145,10 +147,10 @@ extern "C" adg_status adg_measure_peak(int kind, double* tflops, double* ms, dou
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return probe_fail(ADG_ERR_CUDA, std::string("device query: ") + cudaGetErrorString(e));
-  // four blocks of 256 threads per SM: 32 warps per SM, eight per sub-partition
-  const int blocks = sms * 4;
+  // eight blocks of 256 threads per SM: 64 warps per SM, sixteen per sub-partition
+  const int blocks = sms * 8;
   // about 50 ms per launch at the nominal rates (FP64 1.25, FP32 75 TFLOP/s)
-  const int iters = (kind == 1) ? 1000000 : (kind == 4 ? 500000 : 16000);
+  const int iters = (kind == 1) ? 500000 : (kind == 4 ? 250000 : 8000);
   double* sink = nullptr;
   cudaStream_t s = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;

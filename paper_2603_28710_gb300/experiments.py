@@ -7,6 +7,10 @@ Setting of Fig. 5: isentropic vortex on [-5, 5]^2, 64^2 quads (G = 4), 256 subdo
 * `error_map` runs one scheme and returns the per-element maximum density error against
   the exact translating vortex, plus its summary numbers (the quantities Fig. 5 (d)-(f)
   shows as colour maps).
+* `convergence_sweep` runs the isentropic vortex on a sequence of meshes with the
+  synchronous, AT and standard delayed fluxes and returns the L2 errors and the observed
+  orders (the degree-4 sweep of the 256^2 configuration: 32^2 .. 512^2, 8x8 subdomains,
+  CAA L = 3, CK4(5)).
 * `stability_limit` bisects the CFL number between a stable and an unstable value: the
   largest CFL number at which the scheme reaches t_final with a finite state.  The paper
   states that at L = 4 the standard-flux scheme becomes unstable at a CFL number at which
@@ -82,3 +86,31 @@ def stability_limit(flux, lo, hi, iters=6, n=64, degree=2, t_final=4.0, P=16, ma
         else:
             hi = mid
     return lo, hi
+
+
+def convergence_sweep(degree=4, meshes=(32, 64, 128, 256, 512), fluxes=("sync", "at", "std"),
+                      P=8, max_delay=3, rk="ck45", cfl=0.1, t_final=1.0, precision="df64"):
+    """L2 errors (density, momentum, energy) against the exact vortex at t_final for every
+    flux and mesh, and the observed orders between successive meshes:
+    {flux: {"n": [...], "steps": [...], "l2": [[3]...], "order": [[3]...]}}."""
+    out = {}
+    for flux in fluxes:
+        rows = {"n": [], "steps": [], "l2": []}
+        for n in meshes:
+            s = adg.Solver(n_elem=(n, n), degree=degree, P=(P, P), max_delay=max_delay, flux=flux,
+                           rk=rk, cfl=cfl, t_end=t_final, precision=precision)
+            try:
+                s.init_vortex()
+                steps = int(round(t_final / s.info()["dt"]))
+                s.step(steps)
+                if not s.check_finite():
+                    raise RuntimeError(f"{flux} {n}^2 diverged")
+                rows["n"].append(n)
+                rows["steps"].append(steps)
+                rows["l2"].append([float(x) for x in s.l2_error_vortex(t_final)])
+            finally:
+                s.close()
+        e = np.array(rows["l2"])
+        rows["order"] = np.log2(e[:-1] / e[1:]).tolist()
+        out[flux] = rows
+    return out
