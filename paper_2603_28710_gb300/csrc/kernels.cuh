@@ -38,6 +38,25 @@ struct Tile {
   static constexpr int THREADS = EPB * ND;
 };
 
+// Element strides (in values) of the volume kernel's shared-memory tiles.  For 4-byte
+// values the stride is padded to be congruent to the node count modulo the 32 banks, so
+// that a warp's consecutive nodes fall into consecutive banks across element boundaries
+// (unpadded, a 2D p=4 FP32 tile put two elements' nodes into the same banks: 2-way
+// conflicts on every store of the pointwise fluxes and the next stage input).
+constexpr int bank_pad(int base, int nd, int bytes) {
+  return bytes == 4 ? ((nd - base) % 32 + 32) % 32 : 0;
+}
+template <int D, int N, typename R>
+constexpr int sf_stride() {  // pointwise fluxes [el][D][NV][ND]
+  return D * (D + 2) * IPow<N, D>::value +
+         bank_pad(D * (D + 2) * IPow<N, D>::value, IPow<N, D>::value, (int)sizeof(R));
+}
+template <int D, int N, typename C>
+constexpr int sx_stride() {  // next stage input [el][NV][ND]
+  return (D + 2) * IPow<N, D>::value +
+         bank_pad((D + 2) * IPow<N, D>::value, IPow<N, D>::value, (int)sizeof(C));
+}
+
 // floor(e / m.n[i]) for 0 <= e < 2^31 (multiply-high by the precomputed inverse)
 __device__ __forceinline__ int mesh_div(const MeshArgs& m, int i, int e) {
   return m.n[i] == 1 ? e : (int)__umul64hi((unsigned long long)(unsigned)e, m.divm[i]);
@@ -216,14 +235,16 @@ __device__ __forceinline__ void store_trace(float2* p, double v) {
 }
 __device__ __forceinline__ void store_trace(float2* p, df64 v) { *p = make_float2(v.hi, v.lo); }
 
-// Traces of a tile of elements held in shared memory sX[el][v][node] (compute type C) -> tr.
+// Traces of a tile of elements held in shared memory sX[el][v][node] (compute type C,
+// element stride SXS) -> tr.
 // FP32 and FP32-pair operators: a thread owns one (direction, side, variable, face node)
 // combination, so its line of nodes, stride and interpolation weights are set up once, and
 // interpolates it for a run of the tile's elements (the runs split the elements when the
 // block has threads to spare); this halves their instruction count in this phase.  The
 // FP64 operator is bound by its FP64 pipe, not by issue, and keeps one flat loop over all
 // (element, face node) items, which spreads the FP64 work over every thread.
-template <int D, int N, typename R, int TT = 128, typename C = R>
+template <int D, int N, typename R, int TT = 128, typename C = R,
+          int SXS = (D + 2) * IPow<N, D>::value>
 __device__ __forceinline__ void write_traces(const MeshArgs& m, const OpTables* tab, const C* sX,
                                              int e0, typename Arith<R>::S* tr) {
   using T = Tile<D, N, TT>;
@@ -244,7 +265,7 @@ __device__ __forceinline__ void write_traces(const MeshArgs& m, const OpTables* 
       const double* tw = side ? tab->Tp : tab->Tm;
       double acc = 0.0;
 #pragma unroll
-      for (int a = 0; a < N; ++a) acc = fma(tw[a], sX[(el * NV + v) * ND + base + a * stride], acc);
+      for (int a = 0; a < N; ++a) acc = fma(tw[a], sX[el * SXS + v * ND + base + a * stride], acc);
       store_trace(tr + ((ds * NV + v) * ne + e) * NF + j, acc);
     }
   } else {
@@ -267,7 +288,7 @@ __device__ __forceinline__ void write_traces(const MeshArgs& m, const OpTables* 
       const int el1 = el0 + RUN < EPB ? el0 + RUN : EPB;
       typename Arith<R>::S* dst = tr + ((ds * NV + v) * ne + e0) * NF + j;
       for (int el = el0; el < el1 && e0 + el < ne; ++el) {
-        const C* x = sX + (el * NV + v) * ND + base;
+        const C* x = sX + el * SXS + v * ND + base;
         typename Arith<C>::Acc acc = acc_zero(typename Arith<C>::Acc());
 #pragma unroll
         for (int a = 0; a < N; ++a) acc = acc_fma(t[a], x[a * stride], acc);
@@ -399,7 +420,7 @@ template <int D, int N, typename R, int TT>
 constexpr size_t vol_flux_bytes() {
   using T = Tile<D, N, TT>;
   return PackedSweeps<D, R>::value ? sizeof(float4) * T::EPB * D * ((T::NV + 1) / 2) * T::ND
-                                   : sizeof(R) * T::EPB * D * T::NV * T::ND;
+                                   : sizeof(R) * T::EPB * sf_stride<D, N, R>();
 }
 
 // Shared memory of the volume kernel: the pointwise fluxes of the tile, then (kStage) the
@@ -438,7 +459,10 @@ __device__ __forceinline__ void vol_body(const VolArgs& A, int tile, unsigned ch
   using S = typename Arith<R>::S;
   using SM = VolSmem<D, N, R, TT, kStage>;
   constexpr int ND = T::ND, NF = T::NF, NV = T::NV, EPB = T::EPB;
-  R* sF = reinterpret_cast<R*>(smem_raw);  // [EPB][D][NV][ND] (packed sweeps: sF4 below)
+  using CT = typename TraceCompute<R>::C;
+  constexpr int SFS = sf_stride<D, N, R>(), SXS = sx_stride<D, N, CT>();
+  static_assert(sizeof(CT) * EPB * SXS <= SM::FLUX, "the next stage input fits the flux area");
+  R* sF = reinterpret_cast<R*>(smem_raw);  // [EPB][D][NV][ND], element stride SFS (packed sweeps: sF4 below)
   double* sW = reinterpret_cast<double*>(smem_raw + SM::W_OFF);  // [NV][THREADS] (kStage)
   S* sQ = reinterpret_cast<S*>(smem_raw + SM::Q_OFF);            // [NV][THREADS] (kStage)
   const int el = threadIdx.x / ND, node = threadIdx.x - el * ND;
@@ -510,7 +534,7 @@ __device__ __forceinline__ void vol_body(const VolArgs& A, int tile, unsigned ch
 #pragma unroll
       for (int d = 0; d < D; ++d)
 #pragma unroll
-        for (int v = 0; v < NV; ++v) sF[((el * D + d) * NV + v) * ND + node] = F[d][v];
+        for (int v = 0; v < NV; ++v) sF[el * SFS + (d * NV + v) * ND + node] = F[d][v];
     }
   }
   __syncthreads();
@@ -549,7 +573,7 @@ __device__ __forceinline__ void vol_body(const VolArgs& A, int tile, unsigned ch
           const R q = Arith<R>::tab(Qd, Qdf, a);
 #pragma unroll
           for (int v = 0; v < NV; ++v)
-            acc[v] = acc_fma(q, sF[((el * D + d) * NV + v) * ND + base + a * stride], acc[v]);
+            acc[v] = acc_fma(q, sF[el * SFS + (d * NV + v) * ND + base + a * stride], acc[v]);
         }
       }
     }
@@ -599,11 +623,11 @@ __device__ __forceinline__ void vol_body(const VolArgs& A, int tile, unsigned ch
   // 4. traces of the next stage input
   if (A.write_traces) {
     __syncthreads();
-    C* sX = reinterpret_cast<C*>(smem_raw);  // reuse: [EPB][NV][ND]
+    C* sX = reinterpret_cast<C*>(smem_raw);  // reuse: [EPB][NV][ND], element stride SXS
 #pragma unroll
-    for (int v = 0; v < NV; ++v) sX[(el * NV + v) * ND + node] = xnext[v];
+    for (int v = 0; v < NV; ++v) sX[el * SXS + v * ND + node] = xnext[v];
     __syncthreads();
-    write_traces<D, N, R, TT, C>(A.m, A.tab, sX, e0, reinterpret_cast<S*>(A.tr));
+    write_traces<D, N, R, TT, C, SXS>(A.m, A.tab, sX, e0, reinterpret_cast<S*>(A.tr));
   }
 }
 
@@ -617,7 +641,7 @@ template <int D, int N> struct VolKernelRegs<D, N, double> {
   static constexpr int value = D == 2 ? ((N == 3 || N == 8) ? 48 : 40) : 56;  // no spills (ptxas)
 };
 template <int D, int N> struct VolKernelRegs<D, N, float> {
-  static constexpr int value = (D == 2 && N != 3 && N != 4) ? 32 : 40;  // no spills (ptxas, sm_103a)
+  static constexpr int value = (D == 2 && N != 3 && N != 4 && N != 6) ? 32 : 40;  // no spills (ptxas, sm_103a)
 };
 
 template <int D, int N, typename R, int TT = 128>
