@@ -295,9 +295,11 @@ adg_status adg_batch_step(adg_batch* b, int n_steps);
  * tiles of about 64, 128 and 256 threads, each launched as one resident wave of persistent
  * blocks and as one block per tile, and with the instances that fill the GPU four times,
  * once, or never given the single-handle volume launch of their own; then the face-flux
- * launch in both shapes; and keeps the fastest; tile_threads (nullable) receives the tile
- * chosen per group in increasing degree.  It overwrites every instance's state (set states
- * afterwards). */
+ * launch in both shapes; and keeps the fastest; finally it times whole steps with the
+ * instances that fill the GPU once over kept in the graph or stepped as separate handles
+ * (single-handle launches, host-side schedule, after the graph's work on the same stream)
+ * and keeps the faster.  tile_threads (nullable) receives the tile chosen per group in
+ * increasing degree.  It overwrites every instance's state (set states afterwards). */
 adg_status adg_batch_autotune(adg_batch* b, int trials, int* tile_threads);
 adg_status adg_batch_get_state(adg_batch* b, int i, double* u, int64_t count, int on_device);
 adg_status adg_batch_info(const adg_batch* b, int i, double* t, int64_t* step, double* dt,

@@ -106,10 +106,12 @@ struct adg_batch {
   std::vector<int64_t> inst_steps;  // steps taken since each instance's state was set
   struct Group {
     int N = 0, tt = 128;
-    std::vector<int> inst;   // all instances of the degree (face-flux launch)
+    std::vector<int> inst;   // all instances of the degree
+    std::vector<int> finst;  // instances in the graph's face-flux launch
     std::vector<int> vinst;  // instances in the persistent volume launch
     std::vector<int> solo;   // instances with a volume launch of their own
-    int* inst_dev = nullptr;
+    std::vector<int> handles;  // instances stepped as separate handles, outside the graph
+    int* inst_dev = nullptr;  // the flux launch's instances (finst)
     int* vinst_dev = nullptr;
     int* voff_dev = nullptr;
     int* foff_dev = nullptr;
@@ -118,6 +120,8 @@ struct adg_batch {
     int vpersist = 1, fpersist = 1;  // one resident wave looping over tiles, or a block per tile
     int solo_waves = 4;  // instances filling the GPU this many times get a volume launch of
                          // their own (0: none do)
+    int handle_waves = 0;  // instances filling the GPU this many times are stepped as
+                           // separate handles (0: none are)
   };
   std::vector<Group> groups;
   cudaGraphExec_t exec = nullptr;
@@ -192,22 +196,32 @@ adg_status layout_group(adg_batch* b, adg_batch::Group& g) {
   const int64_t wave = (int64_t)sms * std::max(1, vocc);
   g.vinst.clear();
   g.solo.clear();
+  g.finst.clear();
+  g.handles.clear();
   for (int i : g.inst) {
     const int64_t tiles = (b->inst[i]->ne + epb - 1) / epb;
+    if (g.handle_waves > 0 && tiles >= g.handle_waves * wave) {
+      g.handles.push_back(i);
+      continue;
+    }
+    g.finst.push_back(i);
     (g.solo_waves > 0 && tiles >= g.solo_waves * wave ? g.solo : g.vinst).push_back(i);
   }
-  std::vector<int> voff(g.vinst.size() + 1), foff(g.inst.size() + 1);
+  std::vector<int> voff(g.vinst.size() + 1), foff(g.finst.size() + 1);
   voff[0] = foff[0] = 0;
   for (size_t k = 0; k < g.vinst.size(); ++k)
     voff[k + 1] = voff[k] + (int)((b->inst[g.vinst[k]]->ne + epb - 1) / epb);
-  for (size_t k = 0; k < g.inst.size(); ++k)
-    foff[k + 1] = foff[k] + b->dim * (int)((b->inst[g.inst[k]]->ne * nf + 255) / 256);
+  for (size_t k = 0; k < g.finst.size(); ++k)
+    foff[k + 1] = foff[k] + b->dim * (int)((b->inst[g.finst[k]]->ne * nf + 255) / 256);
   g.vtotal = voff.back();
   g.ftotal = foff.back();
   g.vgrid = g.vpersist ? persistent_grid(g.vtotal, std::max(1, vocc)) : g.vtotal;
   g.fgrid = g.fpersist ? persistent_grid(g.ftotal, std::max(1, focc)) : g.ftotal;
   if (!g.vinst.empty())
     BCUDA(b, cudaMemcpy(g.vinst_dev, g.vinst.data(), g.vinst.size() * sizeof(int),
+                        cudaMemcpyHostToDevice));
+  if (!g.finst.empty())
+    BCUDA(b, cudaMemcpy(g.inst_dev, g.finst.data(), g.finst.size() * sizeof(int),
                         cudaMemcpyHostToDevice));
   BCUDA(b, cudaMemcpy(g.voff_dev, voff.data(), voff.size() * sizeof(int), cudaMemcpyHostToDevice));
   BCUDA(b, cudaMemcpy(g.foff_dev, foff.data(), foff.size() * sizeof(int), cudaMemcpyHostToDevice));
@@ -218,7 +232,7 @@ BatchGroupArgs group_args(const adg_batch::Group& g, bool vol) {
   BatchGroupArgs a;
   a.inst = vol ? g.vinst_dev : g.inst_dev;
   a.off = vol ? g.voff_dev : g.foff_dev;
-  a.n = (int)(vol ? g.vinst.size() : g.inst.size());
+  a.n = (int)(vol ? g.vinst.size() : g.finst.size());
   a.total = vol ? g.vtotal : g.ftotal;
   return a;
 }
@@ -239,8 +253,9 @@ adg_status enqueue_step(adg_batch* b, cudaStream_t s) {
   BCUDA(b, cudaGetLastError());
   for (int m = 0; m < b->stages; ++m) {
     for (auto& g : b->groups)
-      BCUDA(b, flux_launch(b->prec, b->dim, g.N, b->fa_dev, b->stages, m, group_args(g, false),
-                           g.fgrid, s));
+      if (!g.finst.empty())
+        BCUDA(b, flux_launch(b->prec, b->dim, g.N, b->fa_dev, b->stages, m, group_args(g, false),
+                             g.fgrid, s));
     for (auto& g : b->groups) {
       adg_status st = vol_group(b, g, m, s);
       if (st != ADG_OK) return st;
@@ -304,6 +319,17 @@ adg_status refresh_instance(adg_batch* b, int i) {
   return ADG_OK;
 }
 
+// one step of the instances stepped as separate handles (their own host schedule and
+// single-handle launches, on the batch's stream after the graph's work)
+adg_status step_handles(adg_batch* b) {
+  for (auto& g : b->groups)
+    for (int i : g.handles) {
+      adg_status st = adg_step(b->inst[i], 1);
+      if (st != ADG_OK) return bfail(b, st, adg_last_error(b->inst[i]));
+    }
+  return ADG_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -362,7 +388,6 @@ adg_status adg_batch_create(int n, const adg_mesh* meshes, const int* degrees, c
     if (ce == cudaSuccess) ce = cudaMalloc((void**)&g.vinst_dev, k * sizeof(int));
     if (ce == cudaSuccess) ce = cudaMalloc((void**)&g.voff_dev, (k + 1) * sizeof(int));
     if (ce == cudaSuccess) ce = cudaMalloc((void**)&g.foff_dev, (k + 1) * sizeof(int));
-    if (ce == cudaSuccess) ce = cudaMemcpy(g.inst_dev, g.inst.data(), k * sizeof(int), cudaMemcpyHostToDevice);
     b->groups.push_back(g);
   }
   if (ce != cudaSuccess) {
@@ -409,7 +434,13 @@ adg_status adg_batch_step(adg_batch* b, int n_steps) {
     adg_status st = build_graph(b);
     if (st != ADG_OK) return st;
   }
-  for (int it = 0; it < n_steps; ++it) BCUDA(b, cudaGraphLaunch(b->exec, b->stream));
+  bool graph_work = false;
+  for (auto& g : b->groups) graph_work = graph_work || !g.finst.empty();
+  for (int it = 0; it < n_steps; ++it) {
+    if (graph_work) BCUDA(b, cudaGraphLaunch(b->exec, b->stream));
+    adg_status st = step_handles(b);
+    if (st != ADG_OK) return st;
+  }
   b->steps += n_steps;
   for (int i = 0; i < b->n; ++i) b->inst_steps[i] += n_steps;
   return ADG_OK;
@@ -497,6 +528,43 @@ adg_status adg_batch_autotune(adg_batch* b, int trials, int* tile_threads) {
     if (st != ADG_OK) return st;
     if (tile_threads) tile_threads[gi] = best_tt;
   }
+  // whole steps: the instances that fill the GPU once over either stay in the graph or are
+  // stepped as separate handles (their single-handle launches with host-side schedules),
+  // whichever is faster -- so a batch never runs them slower than separate handles would
+  auto time_steps = [&](float* ms) -> adg_status {
+    drop_graph(b);
+    for (int t = 0; t <= std::max(trials, 5); ++t) {
+      if (t == 1) BCUDA(b, cudaEventRecord(e0, b->stream));
+      adg_status st = adg_batch_step(b, 1);
+      if (st != ADG_OK) return st;
+    }
+    BCUDA(b, cudaEventRecord(e1, b->stream));
+    BCUDA(b, cudaEventSynchronize(e1));
+    BCUDA(b, cudaEventElapsedTime(ms, e0, e1));
+    return ADG_OK;
+  };
+  for (auto& g : b->groups) {
+    float ms_graph = 0.f, ms_handles = 0.f;
+    g.handle_waves = 0;
+    adg_status st = layout_group(b, g);
+    if (st == ADG_OK) st = time_steps(&ms_graph);
+    if (st != ADG_OK) return st;
+    g.handle_waves = 1;
+    st = layout_group(b, g);
+    if (st != ADG_OK) return st;
+    if (g.handles.empty()) {
+      g.handle_waves = 0;
+    } else {
+      st = time_steps(&ms_handles);
+      if (st != ADG_OK) return st;
+      // the graph keeps them only when it is clearly faster (timing noise would otherwise
+      // flip the choice toward a slower shape about half the time)
+      if (ms_graph < 0.99f * ms_handles) g.handle_waves = 0;
+    }
+    st = layout_group(b, g);
+    if (st != ADG_OK) return st;
+  }
+  drop_graph(b);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   // the tuning launches advanced the uniform flow; states must be set again

@@ -419,8 +419,11 @@ template <> struct PackedSweeps<2, df64> { static constexpr bool value = true; }
 template <int D, int N, typename R, int TT>
 constexpr size_t vol_flux_bytes() {
   using T = Tile<D, N, TT>;
-  return PackedSweeps<D, R>::value ? sizeof(float4) * T::EPB * D * ((T::NV + 1) / 2) * T::ND
-                                   : sizeof(R) * T::EPB * sf_stride<D, N, R>();
+  using C = typename TraceCompute<R>::C;
+  const size_t f = PackedSweeps<D, R>::value ? sizeof(float4) * T::EPB * D * ((T::NV + 1) / 2) * T::ND
+                                             : sizeof(R) * T::EPB * sf_stride<D, N, R>();
+  const size_t x = sizeof(C) * T::EPB * sx_stride<D, N, C>();  // reused for the next input
+  return f > x ? f : x;
 }
 
 // Shared memory of the volume kernel: the pointwise fluxes of the tile, then (kStage) the

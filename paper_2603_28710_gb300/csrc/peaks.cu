@@ -29,8 +29,8 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kChains = 12;
 
-// Every chain has its own multiplier and addend, so consecutive FMAs read different
-// registers (one shared operand pair for all chains measured about 4 % lower).
+// Every chain has its own multiplier and addend (the same rate as one shared operand pair
+// on GB300: the FP64 unit, not operand delivery, is the limit).
 __device__ __forceinline__ void dfma_chains(double (&a)[kChains], const double (&b)[kChains],
                                             const double (&c)[kChains], int iters) {
 #pragma unroll 4
