@@ -650,7 +650,8 @@ def measured_peaks(adg):
     """Arithmetic rates of this GPU from the library's probe (adg_measure_peak), TFLOP/s,
     with the SM clock seen during each probe."""
     out = {"sm_mhz": {}}
-    for kind in ("fp64_fma", "fp64_mma", "fp64_fma+mma", "fp32_fma", "fp32x2_fma"):
+    for kind in ("fp64_fma", "fp64_mma", "fp64_fma+mma", "fp64_add", "fp64_mul", "fp32_fma",
+                 "fp32x2_fma"):
         t, _, mhz = adg.measure_peak(kind)
         out[kind] = t
         out["sm_mhz"][kind] = mhz

@@ -255,7 +255,7 @@ adg_status adg_rhs_noalloc(const adg_mesh* mesh, int degree, double gamma, const
  * one instruction kind with every warp slot busy on independent dependency chains:
  *   kind 0: FP64 FMA; 1: FP32 FMA; 2: FP64 tensor MMA (mma.sync m8n8k4 f64);
  *   3: FP64 FMA and FP64 MMA in alternate warps (shows whether the two paths add up);
- *   4: packed FP32x2 FMA.
+ *   4: packed FP32x2 FMA; 5: FP64 add; 6: FP64 multiply (one flop per operation).
  * tflops receives the best of three timed launches (about 50 ms each at the nominal
  * rates) in TFLOP/s (an FMA counts as 2 flops, an m8n8k4 MMA as 512 per warp); ms
  * (nullable) that launch's duration; sm_mhz (nullable) the SM clock during it (clock64

@@ -199,7 +199,8 @@ def host_schedule(flux, delay_mode, max_delay, np_, P, dim, seed, dmax, n0, coun
     return comm, k, dl[:, :nif]
 
 
-PEAK_KINDS = {"fp64_fma": 0, "fp32_fma": 1, "fp64_mma": 2, "fp64_fma+mma": 3, "fp32x2_fma": 4}
+PEAK_KINDS = {"fp64_fma": 0, "fp32_fma": 1, "fp64_mma": 2, "fp64_fma+mma": 3, "fp32x2_fma": 4,
+              "fp64_add": 5, "fp64_mul": 6}
 
 
 def measure_peak(kind):

@@ -9,6 +9,8 @@
 //   kind 2  FP64 tensor MMA (DMMA):        mma.sync m8n8k4 f64, 4 independent accumulators per warp
 //   kind 3  DFMA and DMMA together:        even warps run kind 0, odd warps kind 2
 //   kind 4  packed FP32x2 FMA (FFMA2):     12 independent chains of float2 per thread
+//   kind 5  FP64 add (DADD):               12 independent chains per thread (1 flop each)
+//   kind 6  FP64 multiply (DMUL):          12 independent chains per thread (1 flop each)
 //
 // Kind 3 tells whether the FP64 tensor path adds throughput to the FP64 FMA pipe (its rate
 // is then close to the sum of kinds 0 and 2) or shares it (close to either alone).
@@ -29,8 +31,9 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kChains = 12;
 
-// Every chain has its own multiplier and addend (the same rate as one shared operand pair
-// on GB300: the FP64 unit, not operand delivery, is the limit).
+// Every chain has its own multiplier and addend, held in registers: they depend on the
+// thread, so the compiler cannot make them constant-bank operands (FP64 FMAs with
+// constant-bank operands measured 16 % slower on GB300: 1.006 against 1.193 TFLOP/s).
 __device__ __forceinline__ void dfma_chains(double (&a)[kChains], const double (&b)[kChains],
                                             const double (&c)[kChains], int iters) {
 #pragma unroll 4
@@ -73,7 +76,7 @@ __global__ void __launch_bounds__(kThreads) probe_kernel(int kind, int iters, do
     float a[kChains];
 #pragma unroll
     for (int j = 0; j < kChains; ++j) a[j] = (float)seed * (j + 1) + threadIdx.x * 1e-7f;
-    const float b = 0.999999f, c = 1e-7f;
+    const float b = 0.999999f * (1.0f + threadIdx.x * 1e-9f), c = 1e-7f * (1.0f + blockIdx.x * 1e-9f);
 #pragma unroll 4
     for (int i = 0; i < iters; ++i) {
 #pragma unroll
@@ -88,7 +91,8 @@ __global__ void __launch_bounds__(kThreads) probe_kernel(int kind, int iters, do
 #pragma unroll
     for (int j = 0; j < kChains; ++j)
       a[j] = make_float2((float)seed * (j + 1), (float)seed * (j + 2) + threadIdx.x * 1e-7f);
-    const float2 b = make_float2(0.999999f, 0.999998f), c = make_float2(1e-7f, 2e-7f);
+    const float tv = 1.0f + threadIdx.x * 1e-9f;  // registers, not constant-bank operands
+    const float2 b = make_float2(0.999999f * tv, 0.999998f * tv), c = make_float2(1e-7f * tv, 2e-7f * tv);
     for (int i = 0; i < iters; ++i) {
 #pragma unroll
       for (int j = 0; j < kChains; ++j) a[j] = __ffma2_rn(a[j], b, c);
@@ -97,6 +101,23 @@ __global__ void __launch_bounds__(kThreads) probe_kernel(int kind, int iters, do
 #pragma unroll
     for (int j = 0; j < kChains; ++j) s += a[j].x + a[j].y;
     if (s > 1e30f) sink[blockIdx.x] = s;
+  } else if (kind == 5 || kind == 6) {
+    double a[kChains], b[kChains];
+    const double tv = 1.0 + threadIdx.x * 1e-12;  // per-chain operands in registers
+#pragma unroll
+    for (int j = 0; j < kChains; ++j) {
+      a[j] = seed * (j + 1) + threadIdx.x * 1e-9;
+      b[j] = (kind == 5 ? 1e-12 * (j + 1) : 0.9999999 - 1e-9 * j) * tv;
+    }
+#pragma unroll 4
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+      for (int j = 0; j < kChains; ++j) a[j] = kind == 5 ? a[j] + b[j] : a[j] * b[j];
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < kChains; ++j) s += a[j];
+    if (s > 1e300) sink[blockIdx.x] = s;
   } else if (use_mma) {
     double acc[4][2];
 #pragma unroll
@@ -108,11 +129,12 @@ __global__ void __launch_bounds__(kThreads) probe_kernel(int kind, int iters, do
     if (s > 1e300) sink[blockIdx.x] = s;
   } else {
     double a[kChains], b[kChains], c[kChains];
+    const double tv = 1.0 + threadIdx.x * 1e-12, bv = 1.0 + blockIdx.x * 1e-12;
 #pragma unroll
     for (int j = 0; j < kChains; ++j) {
       a[j] = seed * (j + 1) + threadIdx.x * 1e-9;
-      b[j] = 0.999999 - 1e-7 * j;
-      c[j] = 1e-9 * (j + 1);
+      b[j] = (0.999999 - 1e-7 * j) * tv;
+      c[j] = 1e-9 * (j + 1) * bv;
     }
     dfma_chains(a, b, c, iters);
     double s = 0.0;
@@ -134,6 +156,7 @@ double launch_flops(int kind, int blocks, int iters) {
   const double mma_warp = (double)(iters / 4) * 4 * 512.0;
   switch (kind) {
     case 0: case 1: return warps * fma_warp;
+    case 5: case 6: return warps * fma_warp / 2.0;
     case 4: return warps * fma_warp * 2.0;
     case 2: return warps * mma_warp;
     case 3: return warps / 2 * (fma_warp + mma_warp);
@@ -149,7 +172,7 @@ adg_status probe_fail(adg_status st, const std::string& m) {
 }  // namespace
 
 extern "C" adg_status adg_measure_peak(int kind, double* tflops, double* ms, double* sm_mhz) {
-  if (kind < 0 || kind > 4 || !tflops) return probe_fail(ADG_ERR_INVALID, "bad peak-probe arguments");
+  if (kind < 0 || kind > 6 || !tflops) return probe_fail(ADG_ERR_INVALID, "bad peak-probe arguments");
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
