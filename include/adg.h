@@ -273,7 +273,8 @@ void adg_destroy(adg_solver* s);
 
 /* ---- batched solver ------------------------------------------------------------------ */
 /* Many independent instances (own mesh, degree, subdomains and max_delay; shared flux
- * rule and options) advanced together.  Instances with the same dimension and degree form
+ * rule and options; options.kernel_path is ignored: the batch runs the split path)
+ * advanced together.  Instances with the same dimension and degree form
  * a group: every RK stage runs one persistent face-flux launch and one persistent volume
  * launch per group, and one whole step of all groups is captured once into a CUDA graph
  * and replayed by adg_batch_step.  The schedule of Algorithms 2/3 advances on the device,
