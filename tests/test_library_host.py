@@ -138,3 +138,20 @@ def test_empty_and_null_inputs_without_gpu():
     assert L.adg_checkpoint_restore(None, None, 0) == 1
     L.adg_destroy(None)
     L.adg_batch_destroy(None)
+
+
+def test_meshes_beyond_the_index_range_are_rejected_before_any_allocation():
+    # 32-bit node indexing: (dim+2) * elements * (degree+1)^dim must stay below 2^31; the
+    # check runs before the library touches the GPU (this test needs none)
+    with pytest.raises(adg.AdgError) as e:
+        adg.Solver(n_elem=(8192, 4096), degree=4)     # 4 * 33.5e6 * 25 = 3.4e9 DoF
+    assert e.value.status == 2 and "2^31" in str(e.value)
+    with pytest.raises(adg.AdgError) as e:
+        adg.Solver(dim=3, n_elem=(512, 512, 256), degree=3)
+    assert e.value.status == 2
+    with pytest.raises(adg.AdgError):
+        adg.Solver(n_elem=(8, 8), degree=8)           # degree 1..7 in 2D
+    with pytest.raises(adg.AdgError):
+        adg.Solver(n_elem=(8, 8), P=(2, 2), flux="at", max_delay=16)
+    with pytest.raises(adg.AdgError):
+        adg.Solver(n_elem=(8, 8), P=(2, 2), flux="at", delay_mode="random", random_delay_max=16)
