@@ -109,10 +109,19 @@ __global__ void __launch_bounds__(kThreads) probe_kernel(int kind, int iters, do
       a[j] = seed * (j + 1) + threadIdx.x * 1e-9;
       b[j] = (kind == 5 ? 1e-12 * (j + 1) : 0.9999999 - 1e-9 * j) * tv;
     }
+    // one loop per kind: a select inside the loop would execute both operations
+    if (kind == 5) {
 #pragma unroll 4
-    for (int i = 0; i < iters; ++i) {
+      for (int i = 0; i < iters; ++i) {
 #pragma unroll
-      for (int j = 0; j < kChains; ++j) a[j] = kind == 5 ? a[j] + b[j] : a[j] * b[j];
+        for (int j = 0; j < kChains; ++j) a[j] = a[j] + b[j];
+      }
+    } else {
+#pragma unroll 4
+      for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int j = 0; j < kChains; ++j) a[j] = a[j] * b[j];
+      }
     }
     double s = 0.0;
 #pragma unroll

@@ -129,3 +129,28 @@ def test_fused_checkpoint_continues_on_split_path():
     b.restore(ck)
     b.step(6)
     assert np.array_equal(b.get_state(), ua)
+
+
+def test_fused_handle_switching_to_the_split_path_mid_run():
+    # trace logging and adg_rhs both need every face trace; a fused handle rebuilds them from
+    # the solution before its next split-path step, so its run equals a split-path handle's
+    import torch
+    kw = dict(n_elem=(16, 16), degree=2, P=(4, 4), max_delay=2, flux="at", rk="ck45", dt=3e-3)
+    runs = {}
+    for path in ("split", "fused"):
+        s = adg.Solver(kernel_path=path, **kw)
+        s.init_vortex()
+        s.step(4)
+        u = s.get_state()
+        s.rhs(u)                               # overwrites the current trace buffer
+        s.step(3)
+        rec = s.set_trace_log(None, 0)
+        log = torch.zeros((12, rec), dtype=torch.float64, device="cuda")
+        s.set_trace_log(log, 12)               # logging: the split path for these steps
+        s.step(2)
+        s.set_trace_log(None, 0)
+        s.step(3)                              # back to the handle's own path
+        runs[path] = (s.get_state(), log.cpu().numpy())
+        s.close()
+    assert np.array_equal(runs["split"][0], runs["fused"][0])
+    assert np.array_equal(runs["split"][1], runs["fused"][1])
