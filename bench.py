@@ -92,7 +92,8 @@ def kernel_source_hash(precision):
     from (a profile taken on other sources no longer describes them)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2603_28710_gb300", "csrc")
-    for name in ("adg_internal.h", "arith.cuh", "df64.cuh", "kernels.cuh", f"k_{precision}.cu"):
+    for name in ("adg_internal.h", "arith.cuh", "df64.cuh", "kernels.cuh", f"k_{precision}.cu",
+                 f"kv_{precision}.cu"):
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode())
             h.update(f.read())
@@ -300,6 +301,12 @@ def whole_job_value(work_per_rank_per_step, steps, seconds_max, world):
     return world * work_per_rank_per_step * steps / seconds_max / 1e9
 
 
+def vol_kernel_name(precision, D, N):
+    """The volume/update kernel the default path (ADG_PATH_AUTO) runs for an arithmetic:
+    the element-face kernel for FP32, the split path's volume kernel otherwise."""
+    return f"{'vol_faces_kernel' if precision == 'fp32' else 'vol_kernel'}<{D},{N}>"
+
+
 def roofline_line(precision, D, N, ndof, vol_ms, vol_n, mpk, kernel):
     """Roofline of the volume/update kernel from its average launch time: algorithmic
     flops (FP64 form, bound by the FP64 pipe) or algorithmic HBM bytes (FP32 and FP32-pair
@@ -357,6 +364,8 @@ def variant_run(adg, stream, precision, steps_per, k, warm, dt, flux="at", delay
     prof = s.get_profile()
     s.set_profiling(False)
     ndof = 4 * N_ELEM * N_ELEM * (DEGREE + 1) ** 2
+    if kernel_path == "auto":  # the path the library chose (only the split path launches fluxes)
+        kernel_path = "split" if prof["flux"][1] > 0 else "element"
     info = s.info()
     finite = s.check_finite()
     err = s.l2_error_vortex(info["t"]) if finite else None  # after warm + k + 2 bench steps
@@ -365,7 +374,8 @@ def variant_run(adg, stream, precision, steps_per, k, warm, dt, flux="at", delay
             "vol_ms_per_launch": prof["vol"][0] / max(prof["vol"][1], 1),
             "flux_ms_per_launch": prof["flux"][0] / max(prof["flux"][1], 1),
             "finite": bool(finite),
-            "l2_error_vs_exact": [float(x) for x in err] if finite else None, "t": info["t"]}
+            "l2_error_vs_exact": [float(x) for x in err] if finite else None, "t": info["t"],
+            "kernel_path": kernel_path}
 
 
 def delay_mode_runs(adg, stream, steps_per, k, dt):
@@ -545,8 +555,9 @@ def tgv_run(adg, stream, mpk, flush, k=3, total_steps=100, with_cpu=True):
         out[prec] = {"value": work * k / (ms * 1e-3) / 1e9,
                      "vol_ms_per_launch": vol_ms / max(vol_n, 1),
                      "flux_ms_per_launch": prof["flux"][0] / max(prof["flux"][1], 1),
+                     "kernel_path": "element" if prof["flux"][1] == 0 else "split",
                      "roofline": dict(roofline_line(prec, 3, TGV_DEGREE + 1, ndof, vol_ms, vol_n,
-                                                    mpk, "vol_kernel<3,4>"),
+                                                    mpk, vol_kernel_name(prec, 3, TGV_DEGREE + 1)),
                                       traffic=ncu_traffic(prec, "kernels_3d_traffic"),
                                       traffic_note="ncu capture at 48^3 scaled to 64^3 by the "
                                                    "element count"),
@@ -577,17 +588,21 @@ def tgv_run(adg, stream, mpk, flush, k=3, total_steps=100, with_cpu=True):
             out[prec][f"rel_l2_diff_vs_fp64_after_{total_steps}_steps"] = float(
                 np.linalg.norm(u - u64) / np.linalg.norm(u64))
         del u
-    # the fused per-stage kernel on the same workload (one schedule cycle per form)
-    out["fused_path"] = {}
-    for prec in ("fp64", "df64", "fp32"):
+    # the fused per-stage kernel, and each arithmetic on the path its default does not take
+    # (element path for FP64 and pairs, split path for FP32), on the same workload (one
+    # schedule cycle per form)
+    out["fused_path"], out["other_path"] = {}, {}
+    for key, prec, path in (("fused_path", "fp64", "fused"), ("fused_path", "df64", "fused"),
+                            ("fused_path", "fp32", "fused"), ("other_path", "fp64", "element"),
+                            ("other_path", "df64", "element"), ("other_path", "fp32", "split")):
         s = adg.Solver(dim=3, n_elem=(TGV_N,) * 3, degree=TGV_DEGREE, lo=(0, 0, 0),
                        hi=(2 * np.pi,) * 3, P=(TGV_P,) * 3, max_delay=TGV_L, flux="at", rk="ck45",
-                       cfl=0.1, precision=prec, kernel_path="fused", stream=stream.cuda_stream)
+                       cfl=0.1, precision=prec, kernel_path=path, stream=stream.cuda_stream)
         s.init_tgv(0.1)
         s.step(8)
         ms = sum(timed_steps(s, stream, 1, 8, flush))
         s.close()
-        out["fused_path"][prec] = {"value": work / (ms * 1e-3) / 1e9}
+        out[key][prec] = {"value": work / (ms * 1e-3) / 1e9, "kernel_path": path}
     if with_cpu:
         out["cpu_baseline"] = tgv_cpu_baseline()
     out["workload"] = ("3D Taylor-Green vortex 64^3 hexes p=3 (83.9M DoF), 8x8x8 subdomains, "
@@ -757,7 +772,8 @@ def run_gpu(args, rank, world, local_rank):
     # roofline of the dominant kernel (volume/update kernel)
     vol_ms, vol_n = prof["vol"]
     flux_ms, flux_n = prof["flux"]
-    roof = roofline_line(args.precision, 2, DEGREE + 1, ndof, vol_ms, vol_n, mpk, "vol_kernel<2,5>")
+    roof = roofline_line(args.precision, 2, DEGREE + 1, ndof, vol_ms, vol_n, mpk,
+                         vol_kernel_name(args.precision, 2, DEGREE + 1))
     roof["traffic"] = ncu_traffic(args.precision)
     launches_per_step = (vol_n + flux_n) / max(args.profile_steps, 1)
 
@@ -792,6 +808,13 @@ def run_gpu(args, rank, world, local_rank):
                                                 kernel_path="fused").items()
                    if k in ("value", "vol_ms_per_launch", "l2_error_vs_exact")}
             for prec in ("fp64", "df64", "fp32")}
+        # each arithmetic on the path the default does not take for it (the element path
+        # for FP64 and pairs, the split path for FP32)
+        variants["other_path"] = {
+            prec: {k: v for k, v in variant_run(adg, stream, prec, steps_per, 3, 1, dt,
+                                                kernel_path=path).items()
+                   if k in ("value", "vol_ms_per_launch", "flux_ms_per_launch", "kernel_path")}
+            for prec, path in (("fp64", "element"), ("df64", "element"), ("fp32", "split"))}
 
     batched = None
     if world == 1 and not args.no_batch:

@@ -86,10 +86,14 @@ typedef enum {
 } adg_precision;
 
 typedef enum {
-  ADG_PATH_AUTO = 0,   /* the faster path on GB300: split, for every arithmetic           */
+  ADG_PATH_AUTO = 0,   /* the faster path on GB300 for the arithmetic: ADG_PATH_ELEMENT
+                          for FP32, ADG_PATH_SPLIT for FP64 and FP32 pairs               */
   ADG_PATH_SPLIT = 1,  /* per RK stage a face-flux launch, then a volume/update launch    */
-  ADG_PATH_FUSED = 2   /* per RK stage one launch per tile of elements: face fluxes and
+  ADG_PATH_FUSED = 2,  /* per RK stage one launch per tile of elements: face fluxes and
                           volume/update work together, tiles staged by TMA copies        */
+  ADG_PATH_ELEMENT = 3 /* per RK stage one volume/update launch in which every element
+                          evaluates the numerical flux on each of its own faces from the
+                          stored traces (no face-flux launch, no face-flux array)        */
 } adg_kernel_path;
 
 typedef struct {
@@ -112,9 +116,10 @@ typedef struct {
   adg_precision precision;   /* default ADG_PREC_FP64                                  */
   void* cuda_stream;         /* cudaStream_t to order work on; NULL: the legacy default
                                 stream (the stream torch uses unless told otherwise)     */
-  adg_kernel_path kernel_path; /* kernels of adg_step, default ADG_PATH_AUTO; both paths
+  adg_kernel_path kernel_path; /* kernels of adg_step, default ADG_PATH_AUTO; the paths
                                 give the same results up to rounding (the learned flux
-                                and trace logging always take the split path)            */
+                                always takes the split path, trace logging the split or
+                                element path)                                            */
 } adg_options;
 
 /* Fills *opt with the defaults listed above. */
@@ -273,8 +278,9 @@ void adg_destroy(adg_solver* s);
 
 /* ---- batched solver ------------------------------------------------------------------ */
 /* Many independent instances (own mesh, degree, subdomains and max_delay; shared flux
- * rule and options; options.kernel_path is ignored: the batch runs the split path)
- * advanced together.  Instances with the same dimension and degree form
+ * rule and options; the batched kernels run the split path's element code, and instances
+ * the autotuner leaves to separate stepping take options.kernel_path, ADG_PATH_FUSED read
+ * as ADG_PATH_SPLIT) advanced together.  Instances with the same dimension and degree form
  * a group: every RK stage runs one persistent face-flux launch and one persistent volume
  * launch per group, and one whole step of all groups is captured once into a CUDA graph
  * and replayed by adg_batch_step.  The schedule of Algorithms 2/3 advances on the device,

@@ -20,7 +20,7 @@ FLUX = {"sync": 0, "std": 1, "at": 2, "at_trace": 3, "learned": 4}
 DELAY = {"caa": 0, "random": 1}
 RK = {"rk22": 0, "rk33": 1, "ck45": 2}
 PREC = {"fp64": 0, "fp32": 1, "df64": 2}
-PATH = {"auto": 0, "split": 1, "fused": 2}
+PATH = {"auto": 0, "split": 1, "fused": 2, "element": 3}
 STATUS = {0: "ADG_OK", 1: "ADG_ERR_INVALID", 2: "ADG_ERR_UNSUPPORTED", 3: "ADG_ERR_CUDA",
           4: "ADG_ERR_OOM", 5: "ADG_ERR_NONFINITE", 6: "ADG_ERR_TIMEOUT", 7: "ADG_ERR_STATE"}
 

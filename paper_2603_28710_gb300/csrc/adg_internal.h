@@ -163,6 +163,9 @@ cudaError_t launch_log_traces(int prec, int dim, int N, const void* tr, const in
 cudaError_t launch_trace(int prec, int dim, int N, const TraceArgs& a, cudaStream_t s);
 cudaError_t launch_flux(int prec, int dim, int N, const FluxArgs& a, cudaStream_t s);
 cudaError_t launch_vol(int prec, int dim, int N, const VolArgs& a, cudaStream_t s);
+// Volume kernel with element-local face fluxes (kv_*.cu): a.v the stage (a.v.tr receives
+// the next stage's traces), a.f the face rules, a.tr_in the current traces.
+cudaError_t launch_vol_faces(int prec, int dim, int N, const FusedArgs& a, cudaStream_t s);
 bool kernels_available(int prec, int dim, int N);
 // Fused per-stage kernel (kf_*.cu): tile shape of (dim, N) in elements per direction, and
 // the launch with the TMA tensor maps of w and of the RK register.

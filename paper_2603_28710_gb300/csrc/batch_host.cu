@@ -346,9 +346,10 @@ adg_status adg_batch_create(int n, const adg_mesh* meshes, const int* degrees, c
   adg_options o;
   if (opt) o = *opt;
   else adg_default_options(&o);
-  // the batched kernels run the split path's element code, and so do the instances the
-  // batch steps as separate handles: results equal separate split-path handles bit for bit
-  o.kernel_path = ADG_PATH_SPLIT;
+  // the batched kernels run the split path's element code; the instances the batch steps
+  // as separate handles take the split or element path (both give the split path's bits),
+  // so results equal separate split-path handles bit for bit
+  if (o.kernel_path == ADG_PATH_FUSED) o.kernel_path = ADG_PATH_SPLIT;
   adg_batch* b = new (std::nothrow) adg_batch();
   if (!b) return bfail(nullptr, ADG_ERR_OOM, "host allocation failed");
   b->n = n;

@@ -20,6 +20,19 @@ cudaError_t launch_fused_fp32(int, int, const FusedArgs&, const CUtensorMap&, co
 cudaError_t launch_fused_df64(int, int, const FusedArgs&, const CUtensorMap&, const CUtensorMap&,
                               cudaStream_t);
 
+cudaError_t launch_vol_faces_fp64(int, int, const FusedArgs&, cudaStream_t);
+cudaError_t launch_vol_faces_fp32(int, int, const FusedArgs&, cudaStream_t);
+cudaError_t launch_vol_faces_df64(int, int, const FusedArgs&, cudaStream_t);
+
+cudaError_t launch_vol_faces(int prec, int dim, int N, const FusedArgs& a, cudaStream_t s) {
+  switch (prec) {
+    case 0: return launch_vol_faces_fp64(dim, N, a, s);
+    case 1: return launch_vol_faces_fp32(dim, N, a, s);
+    case 2: return launch_vol_faces_df64(dim, N, a, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_fused(int prec, int dim, int N, const FusedArgs& a, const CUtensorMap& tw,
                          const CUtensorMap& tx, cudaStream_t s) {
   switch (prec) {

@@ -668,7 +668,7 @@ adg_status adg_create(const adg_mesh* mesh, int degree, const int P[3], int max_
   if ((int)o.rk < 0 || (int)o.rk > 2) return fail(nullptr, ADG_ERR_INVALID, "unknown rk scheme");
   if ((int)o.precision < 0 || (int)o.precision > 2)
     return fail(nullptr, ADG_ERR_INVALID, "unknown precision");
-  if ((int)o.kernel_path < 0 || (int)o.kernel_path > 2)
+  if ((int)o.kernel_path < 0 || (int)o.kernel_path > 3)
     return fail(nullptr, ADG_ERR_INVALID, "unknown kernel path");
   if (!(o.gamma > 1.0)) return fail(nullptr, ADG_ERR_INVALID, "gamma must exceed 1");
   if (o.dt <= 0 && !(o.cfl > 0)) return fail(nullptr, ADG_ERR_INVALID, "need dt > 0 or cfl > 0");
@@ -739,6 +739,13 @@ adg_status adg_create(const adg_mesh* mesh, int degree, const int P[3], int max_
   // between the two launches)
   s->fused = flux != ADG_FLUX_LEARNED && fused_tile(s->dim, s->N, s->tile) &&
              o.kernel_path == ADG_PATH_FUSED;
+  // element path on request, and by default for the FP32 operator: it evaluates every
+  // interior face twice, which the FP32 form (bound by memory and issue) affords and the
+  // FP64 and pair forms (bound by the FP64 pipe) do not (measured on GB300: FP32 +2 to
+  // +6 %, FP64 -24 %, pairs -21 % in 2D and -46 % in 3D)
+  s->faces = flux != ADG_FLUX_LEARNED &&
+             (o.kernel_path == ADG_PATH_ELEMENT ||
+              (o.kernel_path == ADG_PATH_AUTO && o.precision == ADG_PREC_FP32));
   for (int d = 0; d < 3; ++d) {
     if (d >= s->dim) s->tile[d] = 1;
     s->ntile[d] = (s->margs.n[d] + s->tile[d] - 1) / s->tile[d];
@@ -804,10 +811,8 @@ adg_status adg_create(const adg_mesh* mesh, int degree, const int P[3], int max_
   alloc((void**)&s->red_partial, (size_t)s->red_blocks * 5 * sizeof(double));
   alloc((void**)&s->red_out, 8 * sizeof(double));
   alloc((void**)&s->flag, sizeof(int));
-  if (s->fused) {
-    alloc(&s->tr_alt, ntr * sb);
-    alloc((void**)&s->kerr, sizeof(int));
-  }
+  if (s->fused || s->faces) alloc(&s->tr_alt, ntr * sb);
+  if (s->fused) alloc((void**)&s->kerr, sizeof(int));
   if (flux != ADG_FLUX_SYNC) {
     alloc((void**)&s->pe_slot, (size_t)s->dim * ne * sizeof(int32_t));
     alloc((void**)&s->pe_iface, (size_t)(s->npe + 1) * sizeof(int32_t));
@@ -829,7 +834,11 @@ adg_status adg_create(const adg_mesh* mesh, int degree, const int P[3], int max_
   if (ce == cudaSuccess)
     ce = cudaMemcpyAsync(s->tab_dev, &s->tab, sizeof(OpTables), cudaMemcpyHostToDevice, s->stream);
   if (ce == cudaSuccess && flux != ADG_FLUX_SYNC) {
-    ce = cudaMemcpyAsync(s->pe_slot, slot_h, (size_t)s->dim * ne * sizeof(int32_t),
+    // levels not yet stored read as zero (and checkpoints copy defined bytes)
+    const size_t ringn = (size_t)s->depth * (flux >= ADG_FLUX_AT_TRACE ? 2 : 1) * s->NV * s->npe * s->NF;
+    ce = cudaMemsetAsync(s->ring, 0, (ringn + 1) * sb, s->stream);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(s->pe_slot, slot_h, (size_t)s->dim * ne * sizeof(int32_t),
                          cudaMemcpyHostToDevice, s->stream);
     if (ce == cudaSuccess && s->npe > 0)
       ce = cudaMemcpyAsync(s->pe_iface, iface_h, (size_t)s->npe * sizeof(int32_t),
@@ -931,6 +940,23 @@ adg_status adg_step(adg_solver* s, int n_steps) {
         fa.head = s->head < 0 ? 0 : s->head;
         fa.uniform_delay = random ? 0 : (comm ? 0 : k);
         fa.step = n;
+      }
+      if (s->faces) {
+        // one launch: face fluxes of every element's faces from the traces in tr, volume
+        // terms, update, next stage's traces into tr_alt
+        FusedArgs ua;
+        std::memset(&ua, 0, sizeof(ua));
+        ua.v = stage_vol_args(s, m);
+        ua.v.tr = s->tr_alt;
+        ua.f = fa;
+        ua.tr_in = s->tr;
+        ADG_CUDA(s, prof_begin(s, 1));
+        ADG_CUDA(s, launch_vol_faces(s->prec, s->dim, s->N, ua, s->stream));
+        ADG_CUDA(s, prof_end(s));
+        void* t = s->tr;
+        s->tr = s->tr_alt;
+        s->tr_alt = t;
+        continue;
       }
       if (use_fused) {
         FusedArgs ua;

@@ -12,6 +12,9 @@
 //                 inverse mass (diagonal for collocated Gauss points; folded into the
 //                 tables), the low-storage RK update (Eq. 10 or the 2N form), and the
 //                 face traces of the next stage input.
+// or one kernel:
+//   vol_faces_kernel : the volume kernel with each element evaluating the numerical flux
+//                 on its own faces from the stored traces (no face-flux array).
 // Index arithmetic is 32-bit: the host rejects meshes with 2^31 or more degrees of freedom.
 #pragma once
 #include <type_traits>
@@ -428,15 +431,33 @@ constexpr size_t vol_flux_bytes() {
 
 // Shared memory of the volume kernel: the pointwise fluxes of the tile, then (kStage) the
 // per-thread staging slots of the RK operands (FP64 solution; stage register in the
-// operator's storage type).  The trace epilogue reuses the flux area.
-template <int D, int N, typename R, int TT, bool kStage>
+// operator's storage type), then (kFaces) the numerical fluxes on every face of every
+// element of the tile, [EPB][D][side][NV][NF] values of R.  The trace epilogue reuses the
+// flux area.
+template <int D, int N, typename R, int TT, bool kStage, bool kFaces = false>
 struct VolSmem {
   using T = Tile<D, N, TT>;
   static constexpr size_t FLUX = vol_flux_bytes<D, N, R, TT>();
   static constexpr size_t W_OFF = (FLUX + 15) / 16 * 16;
   static constexpr size_t Q_OFF = W_OFF + sizeof(double) * T::NV * T::THREADS;
-  static constexpr size_t BYTES =
+  static constexpr size_t STAGED =
       kStage ? Q_OFF + sizeof(typename Arith<R>::S) * T::NV * T::THREADS : FLUX;
+  static constexpr size_t FACE_OFF = (STAGED + 15) / 16 * 16;
+  static constexpr size_t BYTES =
+      kFaces ? FACE_OFF + sizeof(R) * T::EPB * 2 * D * T::NV * T::NF : STAGED;
+};
+
+// Where the volume kernel takes the numerical fluxes of its elements' faces from.
+// SplitFaces: the global flux array the face-flux launch wrote (each face once).
+// ElementFaces: every element evaluates the numerical flux on each of its own faces from
+// the stored traces of the current stage input (each interior face is then evaluated by
+// both of its elements, with the same arguments and code, hence the same bits; ring
+// stores come from the face's low element only).  The next stage's traces then go to a
+// second trace buffer, since neighbouring blocks still read the current ones.
+struct SplitFaces {};
+struct ElementFaces {
+  const FluxArgs& f;  // face rules of the stage (ring, subdomain slots, AT weights)
+  const void* tr;     // traces of the current stage input [d][side][v][e][j]
 };
 
 // The FP32 and FP32-pair forms wait on memory more than on their pipes: they stage their
@@ -456,11 +477,18 @@ __device__ __forceinline__ df64 from_stored(float2 v) { return df64(v.x, v.y); }
 
 // One element tile (tile index `tile`) of the volume/update kernel.  A is read through a
 // reference so the batched kernels can pass per-instance arguments kept in device memory.
-template <int D, int N, typename R, int TT, bool kStage = false>
-__device__ __forceinline__ void vol_body(const VolArgs& A, int tile, unsigned char* smem_raw) {
+template <int D, int N, typename R, int TT>
+__device__ __forceinline__ void element_face_fluxes(const ElementFaces& F, const MeshArgs& m,
+                                                    int e, const int* ec, int el, int node,
+                                                    bool active, unsigned char* face_smem);
+
+template <int D, int N, typename R, int TT, bool kStage = false, typename Faces = SplitFaces>
+__device__ __forceinline__ void vol_body(const VolArgs& A, int tile, unsigned char* smem_raw,
+                                         const Faces& faces = Faces()) {
   using T = Tile<D, N, TT>;
   using S = typename Arith<R>::S;
-  using SM = VolSmem<D, N, R, TT, kStage>;
+  constexpr bool kFaces = std::is_same<Faces, ElementFaces>::value;
+  using SM = VolSmem<D, N, R, TT, kStage, kFaces>;
   constexpr int ND = T::ND, NF = T::NF, NV = T::NV, EPB = T::EPB;
   using CT = typename TraceCompute<R>::C;
   constexpr int SFS = sf_stride<D, N, R>(), SXS = sx_stride<D, N, CT>();
@@ -506,6 +534,7 @@ __device__ __forceinline__ void vol_body(const VolArgs& A, int tile, unsigned ch
       }
     }
     cp_async_commit();
+    if constexpr (kFaces) element_face_fluxes<D, N, R, TT>(faces, A.m, e, ec, el, node, active, smem_raw + SM::FACE_OFF);
     cp_async_wait<1>();
 #pragma unroll
     for (int v = 0; v < NV; ++v)
@@ -513,6 +542,7 @@ __device__ __forceinline__ void vol_body(const VolArgs& A, int tile, unsigned ch
                      : (from_r ? from_stored(sQ[v * T::THREADS + tid])
                                : Arith<R>::from_double(sW[v * T::THREADS + tid]));
   } else {
+    if constexpr (kFaces) element_face_fluxes<D, N, R, TT>(faces, A.m, e, ec, el, node, active, smem_raw + SM::FACE_OFF);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       const int idx = (v * ne + e) * ND + node;
@@ -594,8 +624,15 @@ __device__ __forceinline__ void vol_body(const VolArgs& A, int tile, unsigned ch
                                  A.scaled ? A.tab->Lmsf[d] : A.tab->Lmf[d], ix[d]);
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        const R fhi = Arith<R>::load(fl + ((d * NV + v) * ne + e) * NF + j);
-        const R flo = Arith<R>::load(fl + ((d * NV + v) * ne + elo) * NF + j);
+        R fhi, flo;
+        if constexpr (kFaces) {
+          const R* sFace = reinterpret_cast<const R*>(smem_raw + SM::FACE_OFF);
+          fhi = sFace[(((el * D + d) * 2 + 1) * NV + v) * NF + j];
+          flo = sFace[(((el * D + d) * 2 + 0) * NV + v) * NF + j];
+        } else {
+          fhi = Arith<R>::load(fl + ((d * NV + v) * ne + e) * NF + j);
+          flo = Arith<R>::load(fl + ((d * NV + v) * ne + elo) * NF + j);
+        }
         acc[v] = acc_fma(lm, flo, acc[v]);
         acc[v] = acc_fma(-lp, fhi, acc[v]);
       }
@@ -768,6 +805,58 @@ __device__ __forceinline__ void flux_body(const FluxArgs& A, int bx, int d) {
   for (int v = 0; v < NV; ++v) Arith<R>::store(fl + ((d * NV + v) * ne + e) * NF + j, f[v]);
 }
 
+// Numerical fluxes on the 2D faces of element e (tile slot el) into shared memory
+// [el][d][side][v][j]: the thread of node `node` takes the face nodes node, node + ND, ...
+// Face (d, lo) lies between element lo and its +d neighbour hi; its flux is evaluated from
+// lo's +d trace and hi's -d trace exactly as the face-flux launch evaluates it, so both
+// elements of the face obtain the same value.
+template <int D, int N, typename R, int TT>
+__device__ __forceinline__ void element_face_fluxes(const ElementFaces& F, const MeshArgs& m,
+                                                    int e, const int* ec, int el, int node,
+                                                    bool active, unsigned char* face_smem) {
+  using T = Tile<D, N, TT>;
+  using S = typename Arith<R>::S;
+  constexpr int ND = T::ND, NF = T::NF, NV = T::NV;
+  if (!active) return;
+  const int ne = (int)m.ne;
+  const S* tr = reinterpret_cast<const S*>(F.tr);
+  R* sFace = reinterpret_cast<R*>(face_smem) + el * (2 * D * NV * NF);
+  for (int q = node; q < 2 * D * NF; q += ND) {
+    const int ds = q / NF, j = q - ds * NF;  // ds = 2 d + side (side 1: the +d face)
+    const int d = ds >> 1, side = ds & 1;
+    const int nb = elem_shift(m, e, ec, d, side ? 1 : -1);
+    const int lo = side ? e : nb, hi = side ? nb : e;
+    R wm[NV], wp[NV], f[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      wm[v] = Arith<R>::load(tr + (((d * 2 + 1) * NV + v) * ne + lo) * NF + j);
+      wp[v] = Arith<R>::load(tr + (((d * 2 + 0) * NV + v) * ne + hi) * NF + j);
+    }
+    const int slot = F.f.pe_mode ? F.f.pe_slot[d * ne + lo] : -1;
+    face_flux<D, N, R>(F.f, d, slot, j, wm, wp, side == 1, f);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) sFace[(ds * NV + v) * NF + j] = f[v];
+  }
+}
+
+// One launch per RK stage without the face-flux launch: the volume kernel with every
+// element evaluating the numerical fluxes on its own faces (ElementFaces).  Register
+// budgets: no spills (ptxas sm_103a); the FP32 form measured best at 48 (40 spilled and
+// lost 8 %, 56 gained nothing).
+template <int D, int N, typename R> struct VolFacesRegs { static constexpr int value = D == 2 ? 64 : 72; };
+template <int D, int N> struct VolFacesRegs<D, N, float> { static constexpr int value = 48; };
+template <int D, int N> struct VolFacesRegs<D, N, double> { static constexpr int value = D == 2 ? 72 : 80; };
+
+template <int D, int N, typename R, int TT = 128>
+__global__ void __launch_bounds__(Tile<D, N, TT>::THREADS,
+                                  min_blocks_for(VolFacesRegs<D, N, R>::value,
+                                                 Tile<D, N, TT>::THREADS))
+vol_faces_kernel(const FusedArgs A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  vol_body<D, N, R, TT, VolStages<R>::value, ElementFaces>(A.v, blockIdx.x, smem_raw,
+                                                           ElementFaces{A.f, A.tr_in});
+}
+
 // Register budget of the face-flux kernel (blocks of 256 threads; no spills, ptxas sm_103a).
 template <int D, typename R> struct FluxKernelRegs { static constexpr int value = D == 2 ? 64 : 72; };
 template <int D> struct FluxKernelRegs<D, float> { static constexpr int value = 48; };
@@ -807,6 +896,20 @@ cudaError_t launch_vol_t(const VolArgs& a, cudaStream_t s) {
 }
 
 template <int D, int N, typename R>
+cudaError_t launch_vol_faces_t(const FusedArgs& a, cudaStream_t s) {
+  using T = Tile<D, N>;
+  const int64_t blocks = (a.v.m.ne + T::EPB - 1) / T::EPB;
+  const size_t smem = VolSmem<D, N, R, 128, VolStages<R>::value, true>::BYTES;
+  if (smem > 48 * 1024) {
+    cudaError_t err = cudaFuncSetAttribute(vol_faces_kernel<D, N, R>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+  }
+  vol_faces_kernel<D, N, R><<<(unsigned)blocks, T::THREADS, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int D, int N, typename R>
 cudaError_t launch_flux_t(const FluxArgs& a, cudaStream_t s) {
   constexpr int NF = IPow<N, D - 1>::value;
   const int64_t per_dir = a.m.ne * NF;
@@ -821,6 +924,7 @@ struct Dispatch {
   static cudaError_t run_trace(int dim, int N, const TraceArgs& a, cudaStream_t s);
   static cudaError_t run_flux(int dim, int N, const FluxArgs& a, cudaStream_t s);
   static cudaError_t run_vol(int dim, int N, const VolArgs& a, cudaStream_t s);
+  static cudaError_t run_vol_faces(int dim, int N, const FusedArgs& a, cudaStream_t s);
 };
 
 #define ADG_DISPATCH_BODY(FN, ARGS)                                  \
@@ -856,6 +960,10 @@ cudaError_t Dispatch<R>::run_flux(int dim, int N, const FluxArgs& a, cudaStream_
 template <typename R>
 cudaError_t Dispatch<R>::run_vol(int dim, int N, const VolArgs& a, cudaStream_t s) {
   ADG_DISPATCH_BODY(launch_vol_t, a)
+}
+template <typename R>
+cudaError_t Dispatch<R>::run_vol_faces(int dim, int N, const FusedArgs& a, cudaStream_t s) {
+  ADG_DISPATCH_BODY(launch_vol_faces_t, a)
 }
 
 }  // namespace adg

@@ -30,7 +30,7 @@ struct adg_solver {
   double* w = nullptr;
   void* x = nullptr;         // 2R: r ; 2N: q (operator storage type)
   void* tr = nullptr;        // traces of the current stage input
-  void* tr_alt = nullptr;    // fused path: traces of the next stage input (swapped with tr)
+  void* tr_alt = nullptr;    // fused and element paths: traces of the next stage input (swapped with tr)
   void* fl = nullptr;        // face fluxes
   void* ring = nullptr;      // delayed-flux history
   int32_t* pe_slot = nullptr;
@@ -64,6 +64,7 @@ struct adg_solver {
   int64_t log_cap = 0, log_count = 0;
   // fused per-stage kernel (ADG_PATH_FUSED)
   bool fused = false;          // adg_step takes the fused path
+  bool faces = false;          // adg_step takes the element path (ADG_PATH_ELEMENT)
   bool traces_partial = false; // tr holds only tile-boundary traces (after fused stages)
   int tile[3] = {1, 1, 1}, ntile[3] = {1, 1, 1};
   int tma = 0;                 // tiles staged by TMA tensor copies

@@ -20,7 +20,7 @@ def main(argv=None):
     ap.add_argument("--P", type=int, default=8)
     ap.add_argument("--L", type=int, default=3)
     ap.add_argument("--steps", type=int, default=2)
-    ap.add_argument("--path", default="auto", choices=["auto", "split", "fused"])
+    ap.add_argument("--path", default="auto", choices=["auto", "split", "fused", "element"])
     a = ap.parse_args(argv)
     import torch
     from . import adg
