@@ -278,11 +278,12 @@ void adg_destroy(adg_solver* s);
 
 /* ---- batched solver ------------------------------------------------------------------ */
 /* Many independent instances (own mesh, degree, subdomains and max_delay; shared flux
- * rule and options; the batched kernels run the split path's element code, and instances
- * the autotuner leaves to separate stepping take options.kernel_path, ADG_PATH_FUSED read
- * as ADG_PATH_SPLIT) advanced together.  Instances with the same dimension and degree form
+ * rule and options) advanced together.  Instances with the same dimension and degree form
  * a group: every RK stage runs one persistent face-flux launch and one persistent volume
- * launch per group, and one whole step of all groups is captured once into a CUDA graph
+ * launch per group (with the FP32 operator, unless options.kernel_path is ADG_PATH_SPLIT:
+ * one persistent element-path launch, every element evaluating its own faces' fluxes;
+ * instances the autotuner leaves to separate stepping take options.kernel_path, with
+ * ADG_PATH_FUSED read as ADG_PATH_SPLIT), and one whole step of all groups is captured once into a CUDA graph
  * and replayed by adg_batch_step.  The schedule of Algorithms 2/3 advances on the device,
  * per instance.  Results equal those of separate adg_solver handles bit for bit. */
 typedef struct adg_batch adg_batch;

@@ -419,7 +419,7 @@ class Batch:
 
     def __init__(self, instances, dim=2, flux="at", rk="ck45", dt=0.0, cfl=0.1, gamma=1.4,
                  delay_mode="caa", seed=0, random_delay_max=0, at_np=0, precision="fp32",
-                 stream=None):
+                 stream=None, kernel_path="auto"):
         L = lib()
         n = len(instances)
         meshes = (Mesh * n)()
@@ -443,6 +443,7 @@ class Batch:
         o.rk, o.dt, o.cfl, o.gamma = RK[rk], dt, cfl, gamma
         o.delay_mode, o.seed = DELAY[delay_mode], seed & 0xFFFFFFFFFFFFFFFF
         o.random_delay_max, o.at_np, o.precision = random_delay_max, at_np, PREC[precision]
+        o.kernel_path = PATH[kernel_path]
         if stream is None:
             import torch
             stream = torch.cuda.current_stream().cuda_stream

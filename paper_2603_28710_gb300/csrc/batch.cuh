@@ -96,6 +96,37 @@ batch_vol_kernel(const VolArgs* va, int nstages, int stage, BatchGroupArgs g) {
   }
 }
 
+// Element path of the batch (FP32 operator): the volume kernel with every element
+// evaluating the numerical fluxes on its own faces, reading each instance's stage and face
+// arguments (the face arguments carry the schedule the device advances) from shared
+// memory.  No face-flux launch.
+template <int D, int N, typename R> struct VolFacesBatchRegs { static constexpr int value = D == 2 ? 72 : 80; };
+
+template <int D, int N, typename R, int TT>
+__global__ void __launch_bounds__(Tile<D, N, TT>::THREADS,
+                                  min_blocks_for(VolFacesBatchRegs<D, N, R>::value,
+                                                 Tile<D, N, TT>::THREADS))
+batch_vol_faces_kernel(const VolArgs* va, const FluxArgs* fa, int nstages, int stage,
+                       BatchGroupArgs g) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(16) VolArgs sa;
+  __shared__ __align__(16) FluxArgs sf;
+  __shared__ int soff[kMaxSharedOffsets];
+  const int* off = stage_offsets(g, soff);
+  int cur = -1;  // instance whose arguments sa and sf hold (uniform over the block)
+  for (int vb = blockIdx.x; vb < g.total; vb += gridDim.x) {
+    const int k = find_instance(off, g.n, vb);
+    if (k != cur) {
+      stage_args(&sa, &va[g.inst[k] * nstages + stage]);
+      stage_args(&sf, &fa[g.inst[k] * nstages + stage]);
+      __syncthreads();
+      cur = k;
+    }
+    vol_body<D, N, R, TT, false, ElementFaces>(sa, vb - off[k], smem_raw, ElementFaces{sf, sf.tr});
+    __syncthreads();  // shared memory (and the arguments) are reused by the next virtual block
+  }
+}
+
 // virtual block of instance k: D * blocks_x of it, ordered (d, bx)
 template <int D, int N, typename R>
 __global__ void __launch_bounds__(256)
@@ -140,6 +171,22 @@ struct BatchDispatch {
     batch_vol_kernel<D, N, R, TT><<<grid, T::THREADS, smem, s>>>(va, ns, st, g);
     return cudaGetLastError();
   }
+  template <int D, int N, int TT>
+  static cudaError_t vol_faces_t(const VolArgs* va, const FluxArgs* fa, int ns, int st,
+                                 const BatchGroupArgs& g, int grid, cudaStream_t s, int* occ) {
+    using T = Tile<D, N, TT>;
+    const size_t smem = VolSmem<D, N, R, TT, false, true>::BYTES;
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(batch_vol_faces_kernel<D, N, R, TT>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    if (occ)
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, batch_vol_faces_kernel<D, N, R, TT>,
+                                                           T::THREADS, smem);
+    batch_vol_faces_kernel<D, N, R, TT><<<grid, T::THREADS, smem, s>>>(va, fa, ns, st, g);
+    return cudaGetLastError();
+  }
   template <int D, int N>
   static cudaError_t flux_t(const FluxArgs* fa, int ns, int st, const BatchGroupArgs& g, int grid,
                             cudaStream_t s, int* occ) {
@@ -147,9 +194,21 @@ struct BatchDispatch {
     batch_flux_kernel<D, N, R><<<grid, 256, 0, s>>>(fa, ns, st, g);
     return cudaGetLastError();
   }
+  // fa != nullptr: the element-path kernel (face fluxes from fa's traces; built for the
+  // FP32 operator, the arithmetic whose batches take the element path)
   template <int D, int N>
-  static cudaError_t vol_tt(int tt, const VolArgs* va, int ns, int st, const BatchGroupArgs& g,
-                            int grid, cudaStream_t s, int* occ) {
+  static cudaError_t vol_tt(int tt, const VolArgs* va, const FluxArgs* fa, int ns, int st,
+                            const BatchGroupArgs& g, int grid, cudaStream_t s, int* occ) {
+    if (fa) {
+      if constexpr (std::is_same<R, float>::value) {
+        switch (tt) {
+          case 64: return vol_faces_t<D, N, 64>(va, fa, ns, st, g, grid, s, occ);
+          case 128: return vol_faces_t<D, N, 128>(va, fa, ns, st, g, grid, s, occ);
+          case 256: return vol_faces_t<D, N, 256>(va, fa, ns, st, g, grid, s, occ);
+        }
+      }
+      return cudaErrorInvalidValue;
+    }
     switch (tt) {
       case 64: return vol_t<D, N, 64>(va, ns, st, g, grid, s, occ);
       case 128: return vol_t<D, N, 128>(va, ns, st, g, grid, s, occ);
@@ -157,25 +216,25 @@ struct BatchDispatch {
     }
     return cudaErrorInvalidValue;
   }
-  static cudaError_t vol(int dim, int N, int tt, const VolArgs* va, int ns, int st,
-                         const BatchGroupArgs& g, int grid, cudaStream_t s, int* occ) {
+  static cudaError_t vol(int dim, int N, int tt, const VolArgs* va, const FluxArgs* fa, int ns,
+                         int st, const BatchGroupArgs& g, int grid, cudaStream_t s, int* occ) {
     if (dim == 2) {
       switch (N) {
-        case 2: return vol_tt<2, 2>(tt, va, ns, st, g, grid, s, occ);
-        case 3: return vol_tt<2, 3>(tt, va, ns, st, g, grid, s, occ);
-        case 4: return vol_tt<2, 4>(tt, va, ns, st, g, grid, s, occ);
-        case 5: return vol_tt<2, 5>(tt, va, ns, st, g, grid, s, occ);
-        case 6: return vol_tt<2, 6>(tt, va, ns, st, g, grid, s, occ);
-        case 7: return vol_tt<2, 7>(tt, va, ns, st, g, grid, s, occ);
-        case 8: return vol_tt<2, 8>(tt, va, ns, st, g, grid, s, occ);
+        case 2: return vol_tt<2, 2>(tt, va, fa, ns, st, g, grid, s, occ);
+        case 3: return vol_tt<2, 3>(tt, va, fa, ns, st, g, grid, s, occ);
+        case 4: return vol_tt<2, 4>(tt, va, fa, ns, st, g, grid, s, occ);
+        case 5: return vol_tt<2, 5>(tt, va, fa, ns, st, g, grid, s, occ);
+        case 6: return vol_tt<2, 6>(tt, va, fa, ns, st, g, grid, s, occ);
+        case 7: return vol_tt<2, 7>(tt, va, fa, ns, st, g, grid, s, occ);
+        case 8: return vol_tt<2, 8>(tt, va, fa, ns, st, g, grid, s, occ);
       }
     } else if (dim == 3) {
       switch (N) {
-        case 2: return vol_tt<3, 2>(tt, va, ns, st, g, grid, s, occ);
-        case 3: return vol_tt<3, 3>(tt, va, ns, st, g, grid, s, occ);
-        case 4: return vol_tt<3, 4>(tt, va, ns, st, g, grid, s, occ);
-        case 5: return vol_tt<3, 5>(tt, va, ns, st, g, grid, s, occ);
-        case 6: return vol_tt<3, 6>(tt, va, ns, st, g, grid, s, occ);
+        case 2: return vol_tt<3, 2>(tt, va, fa, ns, st, g, grid, s, occ);
+        case 3: return vol_tt<3, 3>(tt, va, fa, ns, st, g, grid, s, occ);
+        case 4: return vol_tt<3, 4>(tt, va, fa, ns, st, g, grid, s, occ);
+        case 5: return vol_tt<3, 5>(tt, va, fa, ns, st, g, grid, s, occ);
+        case 6: return vol_tt<3, 6>(tt, va, fa, ns, st, g, grid, s, occ);
       }
     }
     return cudaErrorInvalidValue;

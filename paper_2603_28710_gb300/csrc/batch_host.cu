@@ -17,9 +17,9 @@
 #include "solver_internal.h"
 
 namespace adg {
-cudaError_t batch_vol_fp64(int, int, int, const VolArgs*, int, int, const BatchGroupArgs&, int, cudaStream_t, int*);
-cudaError_t batch_vol_fp32(int, int, int, const VolArgs*, int, int, const BatchGroupArgs&, int, cudaStream_t, int*);
-cudaError_t batch_vol_df64(int, int, int, const VolArgs*, int, int, const BatchGroupArgs&, int, cudaStream_t, int*);
+cudaError_t batch_vol_fp64(int, int, int, const VolArgs*, const FluxArgs*, int, int, const BatchGroupArgs&, int, cudaStream_t, int*);
+cudaError_t batch_vol_fp32(int, int, int, const VolArgs*, const FluxArgs*, int, int, const BatchGroupArgs&, int, cudaStream_t, int*);
+cudaError_t batch_vol_df64(int, int, int, const VolArgs*, const FluxArgs*, int, int, const BatchGroupArgs&, int, cudaStream_t, int*);
 cudaError_t batch_flux_fp64(int, int, const FluxArgs*, int, int, const BatchGroupArgs&, int, cudaStream_t, int*);
 cudaError_t batch_flux_fp32(int, int, const FluxArgs*, int, int, const BatchGroupArgs&, int, cudaStream_t, int*);
 cudaError_t batch_flux_df64(int, int, const FluxArgs*, int, int, const BatchGroupArgs&, int, cudaStream_t, int*);
@@ -60,13 +60,15 @@ __global__ void batch_schedule_kernel(BatchSched* sc, FluxArgs* fa, int nstages,
   sc[i] = s;
 }
 
-// occ != nullptr: no launch, *occ = resident blocks per SM of the kernel
-cudaError_t vol_launch(int prec, int dim, int N, int tt, const VolArgs* va, int ns, int st,
-                       const BatchGroupArgs& g, int grid, cudaStream_t s, int* occ = nullptr) {
+// occ != nullptr: no launch, *occ = resident blocks per SM of the kernel; fa != nullptr:
+// the element-path kernel (face fluxes evaluated in the volume launch)
+cudaError_t vol_launch(int prec, int dim, int N, int tt, const VolArgs* va, const FluxArgs* fa,
+                       int ns, int st, const BatchGroupArgs& g, int grid, cudaStream_t s,
+                       int* occ = nullptr) {
   switch (prec) {
-    case 0: return batch_vol_fp64(dim, N, tt, va, ns, st, g, grid, s, occ);
-    case 1: return batch_vol_fp32(dim, N, tt, va, ns, st, g, grid, s, occ);
-    case 2: return batch_vol_df64(dim, N, tt, va, ns, st, g, grid, s, occ);
+    case 0: return batch_vol_fp64(dim, N, tt, va, fa, ns, st, g, grid, s, occ);
+    case 1: return batch_vol_fp32(dim, N, tt, va, fa, ns, st, g, grid, s, occ);
+    case 2: return batch_vol_df64(dim, N, tt, va, fa, ns, st, g, grid, s, occ);
   }
   return cudaErrorInvalidValue;
 }
@@ -104,6 +106,13 @@ struct adg_batch {
   std::vector<BatchSched> sc_host;
   std::vector<char> has_state;
   std::vector<int64_t> inst_steps;  // steps taken since each instance's state was set
+  // element path (FP32 operator): one volume launch per group and stage, every element
+  // evaluating the fluxes on its own faces; no face-flux launch.  Traces cycle through the
+  // instance's two trace buffers and, for an odd stage count, a third one (tr3), so that
+  // every step ends with the current traces in the instance's own buffer again and the
+  // graph's per-stage arguments stay fixed.
+  bool faces = false;
+  std::vector<void*> tr3;
   struct Group {
     int N = 0, tt = 128;
     std::vector<int> inst;   // all instances of the degree
@@ -161,6 +170,8 @@ void free_batch(adg_batch* b) {
     if (g.voff_dev) cudaFree(g.voff_dev);
     if (g.foff_dev) cudaFree(g.foff_dev);
   }
+  for (void* p : b->tr3)
+    if (p) cudaFree(p);
   if (b->va_dev) cudaFree(b->va_dev);
   if (b->fa_dev) cudaFree(b->fa_dev);
   if (b->sc_dev) cudaFree(b->sc_dev);
@@ -189,7 +200,9 @@ adg_status layout_group(adg_batch* b, adg_batch::Group& g) {
   const int nd = ipow(g.N, b->dim), nf = nd / g.N;
   const int epb = std::max(1, g.tt / nd);
   int vocc = 0, focc = 0, dev = 0, sms = 152;
-  BCUDA(b, vol_launch(b->prec, b->dim, g.N, g.tt, nullptr, 0, 0, BatchGroupArgs{}, 0, 0, &vocc));
+  // (a non-null flux pointer selects the element-path kernel; nothing is launched)
+  BCUDA(b, vol_launch(b->prec, b->dim, g.N, g.tt, nullptr, b->faces ? b->fa_dev : nullptr, 0, 0,
+                      BatchGroupArgs{}, 0, 0, &vocc));
   BCUDA(b, flux_launch(b->prec, b->dim, g.N, nullptr, 0, 0, BatchGroupArgs{}, 0, 0, &focc));
   if (cudaGetDevice(&dev) == cudaSuccess)
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -205,7 +218,8 @@ adg_status layout_group(adg_batch* b, adg_batch::Group& g) {
       continue;
     }
     g.finst.push_back(i);
-    (g.solo_waves > 0 && tiles >= g.solo_waves * wave ? g.solo : g.vinst).push_back(i);
+    // (the element path has no solo launches: its face rules live in device memory)
+    (!b->faces && g.solo_waves > 0 && tiles >= g.solo_waves * wave ? g.solo : g.vinst).push_back(i);
   }
   std::vector<int> voff(g.vinst.size() + 1), foff(g.finst.size() + 1);
   voff[0] = foff[0] = 0;
@@ -240,8 +254,8 @@ BatchGroupArgs group_args(const adg_batch::Group& g, bool vol) {
 // volume work of a group at stage m: the persistent launch and the solo launches
 adg_status vol_group(adg_batch* b, adg_batch::Group& g, int m, cudaStream_t s) {
   if (!g.vinst.empty())
-    BCUDA(b, vol_launch(b->prec, b->dim, g.N, g.tt, b->va_dev, b->stages, m, group_args(g, true),
-                        g.vgrid, s));
+    BCUDA(b, vol_launch(b->prec, b->dim, g.N, g.tt, b->va_dev, b->faces ? b->fa_dev : nullptr,
+                        b->stages, m, group_args(g, true), g.vgrid, s));
   for (int i : g.solo)
     BCUDA(b, launch_vol(b->prec, b->dim, g.N, b->va_host[i * b->stages + m], s));
   return ADG_OK;
@@ -253,7 +267,7 @@ adg_status enqueue_step(adg_batch* b, cudaStream_t s) {
   BCUDA(b, cudaGetLastError());
   for (int m = 0; m < b->stages; ++m) {
     for (auto& g : b->groups)
-      if (!g.finst.empty())
+      if (!g.finst.empty() && !b->faces)
         BCUDA(b, flux_launch(b->prec, b->dim, g.N, b->fa_dev, b->stages, m, group_args(g, false),
                              g.fgrid, s));
     for (auto& g : b->groups) {
@@ -294,6 +308,24 @@ adg_status refresh_instance(adg_batch* b, int i) {
   for (int m = 0; m < b->stages; ++m) {
     b->va_host[i * b->stages + m] = stage_vol_args(s, m);
     b->fa_host[i * b->stages + m] = stage_flux_args(s, m);
+  }
+  if (b->faces) {
+    // stage m reads the traces in X[in(m)] and writes the next stage's into X[out(m)]:
+    // X0 -> X1 -> X0 -> ... and, for an odd stage count, X1 -> X2 -> X0 at the end
+    void* X[3] = {s->tr, s->tr_alt, b->tr3[i]};
+    const int S = b->stages;
+    for (int m = 0; m < S; ++m) {
+      int in = m & 1, out = (m + 1) & 1;
+      if (S & 1) {
+        if (m == S - 2) out = 2;
+        if (m == S - 1) {
+          in = 2;
+          out = 0;
+        }
+      }
+      b->fa_host[i * S + m].tr = X[in];
+      b->va_host[i * S + m].tr = X[out];
+    }
   }
   BatchSched sc;
   std::memset(&sc, 0, sizeof(sc));
@@ -373,6 +405,10 @@ adg_status adg_batch_create(int n, const adg_mesh* meshes, const int* degrees, c
     b->inst.push_back(s);
   }
   b->stages = b->inst[0]->stages;
+  // the FP32 operator takes the element path unless the split path was asked for (the
+  // instance handles then hold their second trace buffer)
+  b->faces = o.precision == ADG_PREC_FP32 && o.kernel_path != ADG_PATH_SPLIT;
+  b->tr3.assign(n, nullptr);
   b->va_host.resize((size_t)n * b->stages);
   b->fa_host.resize((size_t)n * b->stages);
   b->sc_host.resize(n);
@@ -383,6 +419,11 @@ adg_status adg_batch_create(int n, const adg_mesh* meshes, const int* degrees, c
   cudaError_t ce = cudaMalloc((void**)&b->va_dev, sizeof(VolArgs) * n * b->stages);
   if (ce == cudaSuccess) ce = cudaMalloc((void**)&b->fa_dev, sizeof(FluxArgs) * n * b->stages);
   if (ce == cudaSuccess) ce = cudaMalloc((void**)&b->sc_dev, sizeof(BatchSched) * n);
+  for (int i = 0; i < n && ce == cudaSuccess && b->faces && (b->stages & 1); ++i) {
+    const adg_solver* si = b->inst[i];
+    const size_t ntr = (size_t)2 * si->dim * si->NV * si->ne * si->NF;
+    ce = cudaMalloc(&b->tr3[i], ntr * storage_bytes(b->prec));
+  }
   for (auto& kv : by_n) {
     adg_batch::Group g;
     g.N = kv.first;
@@ -496,9 +537,11 @@ adg_status adg_batch_autotune(adg_batch* b, int trials, int* tile_threads) {
     // volume kernel: tile size x launch shape x which instances run the single-handle
     // launch (those filling the GPU 1 or 4 times over, or none)
     const int solo_cand[3] = {4, 1, 0};
+    const int nsolo = b->faces ? 1 : 3;  // the element path has no solo launches
     for (int tt : cand)
       for (int vp = 1; vp >= 0; --vp)
-        for (int sw : solo_cand) {
+        for (int si = 0; si < nsolo; ++si) {
+          const int sw = solo_cand[si];
           g.tt = tt;
           g.vpersist = vp;
           g.solo_waves = sw;
@@ -515,9 +558,9 @@ adg_status adg_batch_autotune(adg_batch* b, int trials, int* tile_threads) {
     g.tt = best_tt;
     g.vpersist = best_vp;
     g.solo_waves = best_sw;
-    // face-flux kernel: launch shape
+    // face-flux kernel: launch shape (none on the element path)
     best = 1e30f;
-    for (int fp = 1; fp >= 0; --fp) {
+    for (int fp = 1; fp >= 0 && !b->faces; --fp) {
       g.fpersist = fp;
       adg_status st = layout_group(b, g);
       if (st == ADG_OK) st = time_group(g, false, &ms);

@@ -3,9 +3,9 @@
 
 namespace adg {
 
-cudaError_t batch_vol_fp64(int dim, int N, int tt, const VolArgs* va, int ns, int st,
-                              const BatchGroupArgs& g, int grid, cudaStream_t s, int* occ) {
-  return BatchDispatch<double>::vol(dim, N, tt, va, ns, st, g, grid, s, occ);
+cudaError_t batch_vol_fp64(int dim, int N, int tt, const VolArgs* va, const FluxArgs* fa, int ns,
+                              int st, const BatchGroupArgs& g, int grid, cudaStream_t s, int* occ) {
+  return BatchDispatch<double>::vol(dim, N, tt, va, fa, ns, st, g, grid, s, occ);
 }
 cudaError_t batch_flux_fp64(int dim, int N, const FluxArgs* fa, int ns, int st,
                                const BatchGroupArgs& g, int grid, cudaStream_t s, int* occ) {

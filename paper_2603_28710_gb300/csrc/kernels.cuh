@@ -111,8 +111,7 @@ __device__ __forceinline__ void euler_flux_all(const R (&w)[D + 2], R gm1, R (&F
     F[d][0] = w[1 + d];
 #pragma unroll
     for (int c = 0; c < D; ++c)  // rho u_c u_d is symmetric: each product once
-      F[d][1 + c] = c < d ? F[c][1 + d] : w[1 + c] * u[d];
-    F[d][1 + d] = F[d][1 + d] + p;
+      F[d][1 + c] = c < d ? F[c][1 + d] : (c == d ? r_fma(w[1 + c], u[d], p) : w[1 + c] * u[d]);
     F[d][D + 1] = ep * u[d];
   }
 }
@@ -123,24 +122,21 @@ template <int D, typename R>
 __device__ __forceinline__ void side_flux(const R (&w)[D + 2], int d, R gamma, R gm1,
                                           R (&fd)[D + 2], R& s2) {
   const R irho = r_rcp(w[0]);
-  R u2 = R(0.0f), ud = R(0.0f), md = w[1];
+  R k2 = R(0.0f), ud = R(0.0f), md = w[1];
 #pragma unroll
   for (int c = 0; c < D; ++c) {
     const R uc = w[1 + c] * irho;
-    u2 = r_fma(uc, uc, u2);
+    k2 = r_fma(w[1 + c], uc, k2);  // rho |u|^2
     if (c == d) {
       ud = uc;
       md = w[1 + c];
     }
   }
-  const R p = gm1 * sub_half(w[D + 1], w[0] * u2);  // (gamma - 1) (E - rho |u|^2 / 2)
-  s2 = r_fma(gamma * p, irho, u2);                  // |u|^2 + gamma p / rho
+  const R p = gm1 * sub_half(w[D + 1], k2);  // (gamma - 1) (E - rho |u|^2 / 2)
+  s2 = r_fma(gamma, p, k2) * irho;           // |u|^2 + gamma p / rho
   fd[0] = md;
 #pragma unroll
-  for (int c = 0; c < D; ++c) {
-    fd[1 + c] = w[1 + c] * ud;
-    if (c == d) fd[1 + c] = fd[1 + c] + p;
-  }
+  for (int c = 0; c < D; ++c) fd[1 + c] = c == d ? r_fma(w[1 + c], ud, p) : w[1 + c] * ud;
   fd[D + 1] = (w[D + 1] + p) * ud;
 }
 

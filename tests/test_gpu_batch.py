@@ -1,8 +1,10 @@
 """Batched solver (adg_batch_*): many uneven vortex instances in one CUDA-graph step.
 
 The batched kernels run the single-instance element code of the split path (face-flux
-launch + volume launch), so every instance must equal a separate split-path solver handle
-bit for bit; one small instance is also checked against the oracle.
+launch + volume launch) or, for the FP32 operator by default, of the element path (one
+volume launch whose elements evaluate their own faces' fluxes; same bits), so every
+instance must equal a separate split-path solver handle bit for bit; one small instance is
+also checked against the oracle.
 """
 import numpy as np
 import pytest
@@ -100,8 +102,8 @@ def test_sixty_four_uneven_vortex_instances():
     for i, s in enumerate(specs):
         b.init_vortex(i, beta=s["beta"], x0=s["x0"], y0=s["y0"])
     b.step(6)
-    # the largest instances get volume launches of their own inside the step's graph, the
-    # others share the persistent launch: compare one of each kind, and the ends
+    # the tuner may step the largest instances as separate handles while the others share
+    # the graph's persistent launches: compare one of each size, and the ends
     big = next(i for i, s in enumerate(specs) if s["n"] == 256)
     small = next(i for i, s in enumerate(specs) if s["n"] == 32)
     for i in sorted({0, 17, 63, big, small}):
@@ -114,3 +116,44 @@ def test_sixty_four_uneven_vortex_instances():
         assert np.array_equal(b.get_state(i), one.get_state())
     for i in range(64):
         assert np.isfinite(b.get_state(i)).all()
+
+
+@pytest.mark.parametrize("rk", ["rk22", "rk33", "ck45"])
+@pytest.mark.parametrize("path", ["auto", "split"])
+def test_fp32_batch_paths_equal_separate_solvers(rk, path):
+    # FP32: the element path by default (traces cycling through two buffers for an even
+    # stage count, three for an odd one, back to the instance's own at the end of a step),
+    # the split path on request; both give the split path's bits
+    kw = dict(flux="at", rk=rk, cfl=0.1, precision="fp32")
+    b = adg.Batch(INSTANCES, kernel_path=path, **kw)
+    for i, ins in enumerate(INSTANCES):
+        b.init_vortex(i, beta=ins["beta"], x0=ins["x0"], y0=ins["y0"])
+    b.step(5)
+    b.step(6)
+    ref = singles_after(INSTANCES, 11, **kw)
+    for i in range(len(INSTANCES)):
+        assert np.array_equal(b.get_state(i), ref[i]), f"instance {i}"
+    b.close()
+
+
+def test_fp32_element_batch_after_autotune():
+    # the tuner's separate-handle trials step instances on the element path (which swaps the
+    # handle's trace buffers); states set afterwards give the batch its buffers back
+    specs = vortex_instances(12, seed=5)
+    insts = [dict(n_elem=(s["n"], s["n"]), degree=s["degree"], P=(8, 8), max_delay=s["max_delay"])
+             for s in specs]
+    kw = dict(flux="at", rk="ck45", cfl=0.1, precision="fp32")
+    b = adg.Batch(insts, **kw)
+    b.autotune(trials=2)
+    for i, s in enumerate(specs):
+        b.init_vortex(i, beta=s["beta"], x0=s["x0"], y0=s["y0"])
+    b.step(3)
+    b.step(4)
+    for i, s in enumerate(specs):
+        one = adg.Solver(n_elem=(s["n"], s["n"]), degree=s["degree"], P=(8, 8),
+                         max_delay=s["max_delay"], kernel_path="split", **kw)
+        one.init_vortex(beta=s["beta"], x0=s["x0"], y0=s["y0"])
+        one.step(7)
+        assert np.array_equal(b.get_state(i), one.get_state()), f"instance {i}"
+        one.close()
+    b.close()
