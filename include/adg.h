@@ -49,7 +49,7 @@ typedef enum {
   ADG_ERR_CUDA = 3,        /* a CUDA runtime call failed; see adg_last_error             */
   ADG_ERR_OOM = 4,         /* device allocation failed                                   */
   ADG_ERR_NONFINITE = 5,   /* the state holds NaN or Inf (adg_check_finite)              */
-  ADG_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up (fused path)            */
+  ADG_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up (fused / element path)  */
   ADG_ERR_STATE = 7        /* call out of order (e.g. adg_step before adg_set_state)      */
 } adg_status;
 
@@ -158,8 +158,9 @@ adg_status adg_init_tgv(adg_solver* s, double mach);
 adg_status adg_step(adg_solver* s, int n_steps);
 
 /* Copies the current state out (waits for the stream).  count must equal n_dof.
- * ADG_ERR_TIMEOUT if a fused-path kernel gave up waiting for the TMA copies of its tile
- * (each wait is limited to about one second; the state is then not valid). */
+ * ADG_ERR_TIMEOUT if a fused-path or element-path kernel gave up waiting for the TMA
+ * copies of its tile (each wait is limited to about one second; the state is then not
+ * valid). */
 adg_status adg_get_state(adg_solver* s, double* u, int64_t count, int on_device);
 
 /* Synchronous DG operator k = M^{-1} L_h(u) (Eq. 7; every face with current data) for an
@@ -268,6 +269,17 @@ adg_status adg_rhs_noalloc(const adg_mesh* mesh, int degree, double gamma, const
  * device buffer and a private stream; waits for its own launches.  Errors:
  * ADG_ERR_INVALID, ADG_ERR_CUDA (adg_last_error(NULL) has the text). */
 adg_status adg_measure_peak(int kind, double* tflops, double* ms, double* sm_mhz);
+
+/* Check of the bounded device-side wait (no counterpart in the paper).  The fused and
+ * element-path kernels wait for their tiles' TMA copies on an mbarrier for at most about
+ * one second and then set an error flag (ADG_ERR_TIMEOUT from adg_get_state) instead of
+ * hanging.  This probe runs the same wait, with limit_cycles SM clock cycles
+ * (0 < limit_cycles <= 4e9), in one block of 128 threads on a barrier that nothing arrives
+ * at: *threads_gave_up receives the number of threads that gave up (128 when the limit
+ * works), *cycles (nullable) the cycles thread 0 waited.  Uses a private stream and a
+ * 16-byte device buffer; waits for its launch.  Errors: ADG_ERR_INVALID, ADG_ERR_CUDA
+ * (adg_last_error(NULL) has the text). */
+adg_status adg_probe_wait(int64_t limit_cycles, int* threads_gave_up, int64_t* cycles);
 
 /* Message for the last failing call on s (NULL: on this thread, for calls without a
  * handle).  Valid until the next call on the same handle/thread. */

@@ -36,7 +36,8 @@ SYMBOLS = ["adg_default_options", "adg_create", "adg_set_state", "adg_init_vorte
            "adg_batch_destroy", "adg_mlp_num_params", "adg_mlp_grad", "adg_mlp_forward",
            "adg_mlp_adam", "adg_mlp_to_bf16", "adg_set_learned_model", "adg_set_trace_log",
            "adg_learned_samples", "adg_host_gauss", "adg_host_at_coeffs",
-           "adg_host_rk", "adg_host_schedule", "adg_host_num_interfaces", "adg_measure_peak"]
+           "adg_host_rk", "adg_host_schedule", "adg_host_num_interfaces", "adg_measure_peak",
+           "adg_probe_wait"]
 
 
 class AdgError(RuntimeError):
@@ -123,6 +124,7 @@ def lib():
             "adg_host_schedule": ([I, I, I, I, I, P, U64, I, I64, I, P, P, P], I),
             "adg_host_num_interfaces": ([I, P], I),
             "adg_measure_peak": ([I, P, P, P], I),
+            "adg_probe_wait": ([I64, P, P], I),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -210,6 +212,14 @@ def measure_peak(kind):
     _check(lib().adg_measure_peak(PEAK_KINDS[kind], ctypes.byref(t), ctypes.byref(ms),
                                   ctypes.byref(mhz)))
     return t.value, ms.value, mhz.value
+
+
+def probe_wait(limit_cycles):
+    """adg_probe_wait: (threads that gave up of 128, cycles thread 0 waited) for a bounded
+    wait on a barrier nothing arrives at."""
+    n, c = ctypes.c_int(), ctypes.c_int64()
+    _check(lib().adg_probe_wait(int(limit_cycles), ctypes.byref(n), ctypes.byref(c)))
+    return n.value, c.value
 
 
 def rhs_noalloc(dim, n_elem, degree, u, k, lo=None, hi=None, gamma=1.4, stream=None):

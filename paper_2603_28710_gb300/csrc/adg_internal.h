@@ -79,6 +79,8 @@ struct __align__(16) VolArgs {
   void* tr;              // traces of the next stage input [d][side][v][e][j]
   int write_traces;
   int scaled;            // 1: use the dt-scaled tables (2N), the accumulator is dt * k
+  int bulk;              // 1: n_elem * nodes is a multiple of 4, so the element path may
+                         // stage whole tiles by TMA bulk copies (16-byte aligned rows)
 };
 
 struct __align__(16) FluxArgs {

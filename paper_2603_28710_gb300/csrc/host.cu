@@ -618,6 +618,7 @@ VolArgs stage_vol_args(const adg_solver* s, int m) {
   va.tr = s->tr;
   va.write_traces = 1;
   va.scaled = s->rk2n ? 1 : 0;
+  va.bulk = (s->ne * s->ND) % 4 == 0 ? 1 : 0;
   return va;
 }
 
@@ -812,7 +813,7 @@ adg_status adg_create(const adg_mesh* mesh, int degree, const int P[3], int max_
   alloc((void**)&s->red_out, 8 * sizeof(double));
   alloc((void**)&s->flag, sizeof(int));
   if (s->fused || s->faces) alloc(&s->tr_alt, ntr * sb);
-  if (s->fused) alloc((void**)&s->kerr, sizeof(int));
+  if (s->fused || s->faces) alloc((void**)&s->kerr, sizeof(int));
   if (flux != ADG_FLUX_SYNC) {
     alloc((void**)&s->pe_slot, (size_t)s->dim * ne * sizeof(int32_t));
     alloc((void**)&s->pe_iface, (size_t)(s->npe + 1) * sizeof(int32_t));
@@ -854,9 +855,9 @@ adg_status adg_create(const adg_mesh* mesh, int degree, const int P[3], int max_
     // defined contents everywhere (checkpoints copy whole trace buffers)
     ce = cudaMemsetAsync(s->tr, 0, ntr * sb, s->stream);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(s->tr_alt, 0, ntr * sb, s->stream);
-    if (ce == cudaSuccess) ce = cudaMemsetAsync(s->kerr, 0, sizeof(int), s->stream);
     s->tma = encode_state_map(s, &s->tm_w, s->w, 8) && encode_state_map(s, &s->tm_x, s->x, (int)sb);
   }
+  if (ce == cudaSuccess && s->kerr) ce = cudaMemsetAsync(s->kerr, 0, sizeof(int), s->stream);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(s->stream);
   delete[] slot_h;
   delete[] iface_h;
@@ -950,6 +951,7 @@ adg_status adg_step(adg_solver* s, int n_steps) {
         ua.v.tr = s->tr_alt;
         ua.f = fa;
         ua.tr_in = s->tr;
+        ua.err = s->kerr;
         ADG_CUDA(s, prof_begin(s, 1));
         ADG_CUDA(s, launch_vol_faces(s->prec, s->dim, s->N, ua, s->stream));
         ADG_CUDA(s, prof_end(s));
@@ -1034,7 +1036,8 @@ adg_status adg_get_state(adg_solver* s, double* u, int64_t count, int on_device)
     int kerr = 0;
     ADG_CUDA(s, cudaMemcpy(&kerr, s->kerr, sizeof(int), cudaMemcpyDeviceToHost));
     if (kerr)
-      return fail(s, ADG_ERR_TIMEOUT, "a fused-kernel wait for its tile copies gave up; the state is not valid");
+      return fail(s, ADG_ERR_TIMEOUT,
+                  "a kernel's wait for its tile copies gave up (fused or element path); the state is not valid");
   }
   return ADG_OK;
 }

@@ -220,6 +220,50 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(n) : "memory");
 }
 
+// ---- mbarrier and TMA bulk copies (PTX) -----------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Waits for phase `parity` of the barrier for at most `limit` SM clock cycles.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, long long limit) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > limit) return false;
+  }
+  return true;
+}
+// 1D bulk copy global -> shared by the TMA engine (both addresses 16-byte aligned, size a
+// multiple of 16 bytes), completion counted on the mbarrier
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// about one second at the GB300 SM clock
+constexpr long long kWaitLimitCycles = 2000000000ll;
+
 // Arithmetic of the trace interpolation for an operator arithmetic R: the FP32-pair kernels
 // interpolate in native FP64 (their FP64 pipe is otherwise idle and the RK update hands
 // over the FP64 stage input), the others in R itself.
@@ -454,6 +498,7 @@ struct SplitFaces {};
 struct ElementFaces {
   const FluxArgs& f;  // face rules of the stage (ring, subdomain slots, AT weights)
   const void* tr;     // traces of the current stage input [d][side][v][e][j]
+  int* err;           // set to 2 when a wait for the tile's bulk copies gave up
 };
 
 // The FP32 and FP32-pair forms wait on memory more than on their pipes: they stage their
@@ -485,6 +530,17 @@ __device__ __forceinline__ void vol_body(const VolArgs& A, int tile, unsigned ch
   using S = typename Arith<R>::S;
   constexpr bool kFaces = std::is_same<Faces, ElementFaces>::value;
   using SM = VolSmem<D, N, R, TT, kStage, kFaces>;
+  // element path with staged operands in 3D: whole tiles are staged by TMA bulk copies (one
+  // per variable row, issued by one thread; rows of whole 16-byte units) instead of one
+  // asynchronous copy per thread and value (64^3 p=3 FP32: 850 -> 832 us per stage).  In 2D
+  // p=4 the rows align only for 16-element tiles, which cost more than the copies save
+  // (205 -> 253 us at 512^2).
+  constexpr bool kBulk = kFaces && kStage && D == 3 && (Tile<D, N, TT>::THREADS % 4 == 0);
+  uint64_t* vbar = nullptr;  // completion barriers of the two copy groups
+  if constexpr (kBulk) {
+    __shared__ __align__(8) uint64_t bars[2];
+    vbar = bars;
+  }
   constexpr int ND = T::ND, NF = T::NF, NV = T::NV, EPB = T::EPB;
   using CT = typename TraceCompute<R>::C;
   constexpr int SFS = sf_stride<D, N, R>(), SXS = sx_stride<D, N, CT>();
@@ -507,12 +563,41 @@ __device__ __forceinline__ void vol_body(const VolArgs& A, int tile, unsigned ch
   const bool from_r = (A.mode == kMode2R && A.stage > 0);
   const S* rin = reinterpret_cast<const S*>(A.r_in);
   const int tid = threadIdx.x;
+  bool bulk = false, group2 = false;  // block-uniform
   if constexpr (kStage) {
     // group 1: the stage input (FP64 solution, or the 2R register r into the q slots);
     // group 2: the solution when the input was r, and the 2N register q
     const bool upd = active && A.mode != kModeRHS;
     const bool want_q = upd && A.mode == kMode2N && A.stage > 0;
-    if (active) {
+    if constexpr (kBulk) bulk = A.bulk && e0 + EPB <= ne;  // a whole tile, aligned rows
+    group2 = upd && (from_r || want_q);
+    if (bulk) {
+      if (tid == 0) {
+        mbar_init(vbar, 1);
+        mbar_init(vbar + 1, 1);
+      }
+      __syncthreads();
+      if (tid == 0) {
+        constexpr unsigned RW = sizeof(double) * T::THREADS, RS = sizeof(S) * T::THREADS;
+        const S* xin = reinterpret_cast<const S*>(A.x);
+        mbar_expect_tx(vbar, NV * (from_r ? RS : RW));
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const int row = (v * ne + e0) * ND;
+          if (from_r) bulk_load(sQ + v * T::THREADS, rin + row, RS, vbar);
+          else bulk_load(sW + v * T::THREADS, A.w_in + row, RW, vbar);
+        }
+        if (group2) {
+          mbar_expect_tx(vbar + 1, NV * ((from_r ? RW : 0u) + (want_q ? RS : 0u)));
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            const int row = (v * ne + e0) * ND;
+            if (from_r) bulk_load(sW + v * T::THREADS, A.w + row, RW, vbar + 1);
+            if (want_q) bulk_load(sQ + v * T::THREADS, xin + row, RS, vbar + 1);
+          }
+        }
+      }
+    } else if (active) {
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         const int idx = (v * ne + e) * ND + node;
@@ -520,8 +605,8 @@ __device__ __forceinline__ void vol_body(const VolArgs& A, int tile, unsigned ch
         else cp_async8(sW + v * T::THREADS + tid, A.w_in + idx);
       }
     }
-    cp_async_commit();
-    if (upd && (from_r || want_q)) {
+    if (!bulk) cp_async_commit();
+    if (!bulk && upd && (from_r || want_q)) {
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         const int idx = (v * ne + e) * ND + node;
@@ -529,9 +614,13 @@ __device__ __forceinline__ void vol_body(const VolArgs& A, int tile, unsigned ch
         if (want_q) cp_async_val(sQ + v * T::THREADS + tid, reinterpret_cast<const S*>(A.x) + idx);
       }
     }
-    cp_async_commit();
+    if (!bulk) cp_async_commit();
     if constexpr (kFaces) element_face_fluxes<D, N, R, TT>(faces, A.m, e, ec, el, node, active, smem_raw + SM::FACE_OFF);
-    cp_async_wait<1>();
+    if (!bulk) {
+      cp_async_wait<1>();
+    } else if constexpr (kBulk) {
+      if (!mbar_wait_bounded(vbar, 0, kWaitLimitCycles)) atomicOr(faces.err, 2);
+    }
 #pragma unroll
     for (int v = 0; v < NV; ++v)
       u[v] = !active ? R(1.0f)
@@ -638,7 +727,13 @@ __device__ __forceinline__ void vol_body(const VolArgs& A, int tile, unsigned ch
   // 3. Runge-Kutta update; xnext = input of the next stage
   using C = typename TraceCompute<R>::C;
   C xnext[NV];
-  if constexpr (kStage) cp_async_wait<0>();
+  if constexpr (kStage) {
+    if (!bulk) {
+      cp_async_wait<0>();
+    } else if constexpr (kBulk) {
+      if (group2 && !mbar_wait_bounded(vbar + 1, 0, kWaitLimitCycles)) atomicOr(faces.err, 2);
+    }
+  }
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     const int idx = (v * ne + e) * ND + node;
@@ -839,7 +934,9 @@ __device__ __forceinline__ void element_face_fluxes(const ElementFaces& F, const
 // element evaluating the numerical fluxes on its own faces (ElementFaces).  Register
 // budgets: no spills (ptxas sm_103a); the FP32 form measured best at 48 (40 spilled and
 // lost 8 %, 56 gained nothing).
-template <int D, int N, typename R> struct VolFacesRegs { static constexpr int value = D == 2 ? 64 : 72; };
+template <int D, int N, typename R> struct VolFacesRegs { static constexpr int value = D == 2 ? 64 : 80; };
+// Threads per block of the element path: tiles of about 128 threads, as in the split path.
+template <int D, int N> struct FacesTT { static constexpr int value = 128; };
 template <int D, int N> struct VolFacesRegs<D, N, float> { static constexpr int value = 48; };
 template <int D, int N> struct VolFacesRegs<D, N, double> { static constexpr int value = D == 2 ? 72 : 80; };
 
@@ -850,7 +947,7 @@ __global__ void __launch_bounds__(Tile<D, N, TT>::THREADS,
 vol_faces_kernel(const FusedArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   vol_body<D, N, R, TT, VolStages<R>::value, ElementFaces>(A.v, blockIdx.x, smem_raw,
-                                                           ElementFaces{A.f, A.tr_in});
+                                                           ElementFaces{A.f, A.tr_in, A.err});
 }
 
 // Register budget of the face-flux kernel (blocks of 256 threads; no spills, ptxas sm_103a).
@@ -893,15 +990,16 @@ cudaError_t launch_vol_t(const VolArgs& a, cudaStream_t s) {
 
 template <int D, int N, typename R>
 cudaError_t launch_vol_faces_t(const FusedArgs& a, cudaStream_t s) {
-  using T = Tile<D, N>;
+  constexpr int TT = FacesTT<D, N>::value;
+  using T = Tile<D, N, TT>;
   const int64_t blocks = (a.v.m.ne + T::EPB - 1) / T::EPB;
-  const size_t smem = VolSmem<D, N, R, 128, VolStages<R>::value, true>::BYTES;
+  const size_t smem = VolSmem<D, N, R, TT, VolStages<R>::value, true>::BYTES;
   if (smem > 48 * 1024) {
-    cudaError_t err = cudaFuncSetAttribute(vol_faces_kernel<D, N, R>,
+    cudaError_t err = cudaFuncSetAttribute(vol_faces_kernel<D, N, R, TT>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
   }
-  vol_faces_kernel<D, N, R><<<(unsigned)blocks, T::THREADS, smem, s>>>(a);
+  vol_faces_kernel<D, N, R, TT><<<(unsigned)blocks, T::THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }
 

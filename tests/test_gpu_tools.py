@@ -36,3 +36,20 @@ def test_peak_probe_rates_are_plausible():
     assert 500.0 < mhz < 3000.0
     assert 20.0 < f32 < 150.0 and f32 > 10 * f64
     assert mma > 0.0 and both > 0.0
+
+
+def test_bounded_wait_gives_up_and_the_context_stays_usable():
+    # the fused and element-path kernels' mbarrier wait, on a barrier nothing arrives at:
+    # every thread gives up after the limit (about 1 ms here), and the device is fine after
+    from paper_2603_28710_gb300 import adg
+    limit = 2_000_000
+    n, cycles = adg.probe_wait(limit)
+    assert n == 128
+    assert limit < cycles < 4 * limit + 1_000_000
+    s = adg.Solver(n_elem=(8, 8), degree=2, P=(2, 2), max_delay=2, flux="at", rk="ck45",
+                   dt=1e-3, precision="fp32", kernel_path="element")
+    s.init_vortex()
+    s.step(3)
+    assert s.check_finite()
+    s.get_state()                       # the element path's error flag is clear
+    s.close()

@@ -98,6 +98,11 @@ def test_bad_arguments_rejected_without_gpu():
         adg.host_gauss(0)
     with pytest.raises(adg.AdgError):
         adg.host_at_coeffs(9, 1.0)
+    # the bounded-wait probe checks its limit before any device work
+    with pytest.raises(adg.AdgError):
+        adg.probe_wait(0)
+    with pytest.raises(adg.AdgError):
+        adg.probe_wait(5_000_000_000)
 
 
 @pytest.mark.parametrize("kw,msg", [
