@@ -564,6 +564,7 @@ __device__ __forceinline__ void vol_body(const VolArgs& A, int tile, unsigned ch
   const S* rin = reinterpret_cast<const S*>(A.r_in);
   const int tid = threadIdx.x;
   bool bulk = false, group2 = false;  // block-uniform
+  bool gave_up = false;               // a bounded wait for the bulk copies ran out
   if constexpr (kStage) {
     // group 1: the stage input (FP64 solution, or the 2R register r into the q slots);
     // group 2: the solution when the input was r, and the 2N register q
@@ -619,7 +620,10 @@ __device__ __forceinline__ void vol_body(const VolArgs& A, int tile, unsigned ch
     if (!bulk) {
       cp_async_wait<1>();
     } else if constexpr (kBulk) {
-      if (!mbar_wait_bounded(vbar, 0, kWaitLimitCycles)) atomicOr(faces.err, 2);
+      if (!mbar_wait_bounded(vbar, 0, kWaitLimitCycles)) {
+        gave_up = true;
+        atomicOr(faces.err, 2);
+      }
     }
 #pragma unroll
     for (int v = 0; v < NV; ++v)
@@ -731,7 +735,10 @@ __device__ __forceinline__ void vol_body(const VolArgs& A, int tile, unsigned ch
     if (!bulk) {
       cp_async_wait<0>();
     } else if constexpr (kBulk) {
-      if (group2 && !mbar_wait_bounded(vbar + 1, 0, kWaitLimitCycles)) atomicOr(faces.err, 2);
+      if (group2 && !mbar_wait_bounded(vbar + 1, 0, kWaitLimitCycles)) {
+        gave_up = true;
+        atomicOr(faces.err, 2);
+      }
     }
   }
 #pragma unroll
@@ -759,6 +766,14 @@ __device__ __forceinline__ void vol_body(const VolArgs& A, int tile, unsigned ch
     for (int v = 0; v < NV; ++v) sX[el * SXS + v * ND + node] = xnext[v];
     __syncthreads();
     write_traces<D, N, R, TT, C, SXS>(A.m, A.tab, sX, e0, reinterpret_cast<S*>(A.tr));
+  }
+  if constexpr (kBulk) {
+    // after a wait that ran out (the results are then flagged as invalid): wait once more,
+    // again bounded, for the tile's copies before the block's shared memory is released
+    if (gave_up) {
+      mbar_wait_bounded(vbar, 0, kWaitLimitCycles);
+      if (group2) mbar_wait_bounded(vbar + 1, 0, kWaitLimitCycles);
+    }
   }
 }
 

@@ -157,3 +157,31 @@ def test_fp32_element_batch_after_autotune():
         assert np.array_equal(b.get_state(i), one.get_state()), f"instance {i}"
         one.close()
     b.close()
+
+
+@pytest.mark.parametrize("precision,rk", [("fp32", "ck45"), ("fp32", "rk22"), ("fp64", "ck45"),
+                                          ("df64", "rk33")])
+def test_3d_batch_equals_separate_solvers(precision, rk):
+    # 3D Taylor-Green instances of degrees 1-3 (FP32: the batched element path; FP64 and
+    # pairs: the split pair), against separate split-path handles, bit for bit
+    box = dict(lo=(0.0, 0.0, 0.0), hi=(2 * np.pi,) * 3)
+    insts = [dict(n_elem=(4, 4, 4), degree=3, P=(2, 2, 2), max_delay=4, **box),
+             dict(n_elem=(6, 4, 2), degree=2, P=(2, 2, 1), max_delay=2, **box),
+             dict(n_elem=(4, 4, 4), degree=2, P=(2, 2, 2), max_delay=3, **box),
+             dict(n_elem=(2, 2, 2), degree=1, P=(1, 1, 1), max_delay=1, **box)]
+    kw = dict(flux="at", rk=rk, cfl=0.1, precision=precision)
+    b = adg.Batch(insts, dim=3, **kw)
+    ones = []
+    for i, ins in enumerate(insts):
+        one = adg.Solver(dim=3, n_elem=ins["n_elem"], degree=ins["degree"], P=ins["P"],
+                         max_delay=ins["max_delay"], lo=box["lo"], hi=box["hi"],
+                         kernel_path="split", **kw)
+        one.init_tgv(0.1)
+        b.set_state(i, one.get_state())
+        ones.append(one)
+    b.step(6)
+    for i, one in enumerate(ones):
+        one.step(6)
+        assert np.array_equal(b.get_state(i), one.get_state()), f"instance {i}"
+        one.close()
+    b.close()
