@@ -333,7 +333,7 @@ void adg_batch_destroy(adg_batch* b);
 /* ---- learned ghost-trace predictor ------------------------------------------------- */
 /* A small MLP (4 -> 64 -> 64 -> 1, tanh hidden layers) with BF16 weights and FP32
  * accumulation, used by ADG_FLUX_LEARNED to correct the AT extrapolation of subdomain
- * traces.  Not part of the paper's method: an add-on whose error is judged against, and
+ * traces.  Not part of the paper's method: an add-on whose error is measured against, and
  * which falls back to, the plain AT extrapolation.  Parameters: adg_mlp_num_params()
  * values laid out W1[64][4] | b1[64] | W2[64][64] | b2[64] | w3[64] | b3.
  * All pointers below are DEVICE pointers; work is enqueued on cuda_stream. */

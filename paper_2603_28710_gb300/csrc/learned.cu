@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(128) learned_features_kernel(const LearnArgs A
 }
 
 // Pass 3 (after the network evaluated y for every channel), thread per (face, face node):
-// corrected traces (the judge keeps E when y is not finite, |y| > trust or s = 0), then
+// corrected traces (the trust test keeps E when y is not finite, |y| > trust or s = 0), then
 // the Rusanov flux of Eq. 8 overwrites the face flux.
 template <int D, int N, typename R>
 __global__ void __launch_bounds__(128) learned_apply_kernel(const LearnArgs A) {

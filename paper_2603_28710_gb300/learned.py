@@ -13,7 +13,7 @@ learned next-order step, kept where |target| <= 2:
             are logged and samples drawn for delays k = 1..4 and every stage;
   model  -- 4 -> 64 -> 64 -> 1 MLP, tanh, BF16 weights / FP32 accumulation; Adam;
   use    -- ADG_FLUX_LEARNED with at_np = 2: correction of the AT trace extrapolation,
-            AT itself as fallback and judge (include/adg.h).
+            AT itself as fallback and arbiter (include/adg.h).
 """
 from __future__ import annotations
 

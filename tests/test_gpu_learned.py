@@ -149,7 +149,7 @@ def test_trained_network_against_plain_at_on_taylor_green():
     # (64^3, p=3, L=4): the gain is e_AT / e_learned (> 1 would be an improvement)
     # Measured: the network does not beat AT here (gain x0.35 at trust 1, x0.68 at 0.05):
     # AT's residual on this smooth flow is far below its own E3 - E2 error estimate, and the
-    # network's prediction noise exceeds it.  The judge bounds the harm: a tight trust
+    # network's prediction noise exceeds it.  The trust test bounds the harm: a tight trust
     # recovers the AT result.
     model, meta = learned.load()
     e_at = _tgv_error("at_trace")
