@@ -950,8 +950,6 @@ __device__ __forceinline__ void element_face_fluxes(const ElementFaces& F, const
 // budgets: no spills (ptxas sm_103a); the FP32 form measured best at 48 (40 spilled and
 // lost 8 %, 56 gained nothing).
 template <int D, int N, typename R> struct VolFacesRegs { static constexpr int value = D == 2 ? 64 : 80; };
-// Threads per block of the element path: tiles of about 128 threads, as in the split path.
-template <int D, int N> struct FacesTT { static constexpr int value = 128; };
 template <int D, int N> struct VolFacesRegs<D, N, float> { static constexpr int value = 48; };
 template <int D, int N> struct VolFacesRegs<D, N, double> { static constexpr int value = D == 2 ? 72 : 80; };
 
@@ -1005,7 +1003,7 @@ cudaError_t launch_vol_t(const VolArgs& a, cudaStream_t s) {
 
 template <int D, int N, typename R>
 cudaError_t launch_vol_faces_t(const FusedArgs& a, cudaStream_t s) {
-  constexpr int TT = FacesTT<D, N>::value;
+  constexpr int TT = 128;  // tiles of about 128 threads, as on the split path
   using T = Tile<D, N, TT>;
   const int64_t blocks = (a.v.m.ne + T::EPB - 1) / T::EPB;
   const size_t smem = VolSmem<D, N, R, TT, VolStages<R>::value, true>::BYTES;
