@@ -65,6 +65,8 @@ struct __align__(16) VolArgs {
   const OpTables* tab;
   double gamma;
   float2 gammaf;   // gamma as an FP32 pair
+  double gm1;      // gamma - 1 (every node's pressure needs it)
+  float2 gm1f;     // gamma - 1 as an FP32 pair
   int mode;        // UpdateMode
   int stage, last; // stage index; last = 1 on the final stage of a step
   double ca, cb;   // 2R: dt*a_m, dt*b_m ; 2N: A_m, B_m
@@ -87,6 +89,8 @@ struct __align__(16) FluxArgs {
   MeshArgs m;
   double gamma;
   float2 gammaf;
+  double gm1;      // gamma - 1 (every face node's pressures need it)
+  float2 gm1f;
   const void* tr;
   void* fl;
   // subdomain-face handling
@@ -132,6 +136,8 @@ struct LearnArgs {
   MeshArgs m;
   double gamma;
   float2 gammaf;
+  double gm1;               // gamma - 1, as in the face-flux arguments
+  float2 gm1f;
   const void* ring;         // trace ring [level][2][v][slot][j]
   void* fl;                 // face fluxes to overwrite on subdomain faces
   const int32_t* face_d;    // [slot] direction

@@ -376,7 +376,7 @@ fused_kernel(const __grid_constant__ FusedArgs A, const __grid_constant__ CUtens
     // ---- B2. pointwise Euler fluxes (over U and T, both no longer needed) -----------------
     {
       R Fp[D][NV];
-      euler_flux_all<D, R>(u, Arith<R>::pair(V.gamma, V.gammaf) - R(1.0f), Fp);
+      euler_flux_all<D, R>(u, Arith<R>::pair(V.gm1, V.gm1f), Fp);
       if constexpr (PK) {
 #pragma unroll
         for (int d = 0; d < D; ++d)

@@ -438,6 +438,8 @@ FluxArgs base_flux_args(adg_solver* s) {
   fa.m = s->margs;
   fa.gamma = s->opt.gamma;
   fa.gammaf = split2(s->opt.gamma);
+  fa.gm1 = s->opt.gamma - 1.0;
+  fa.gm1f = split2(s->opt.gamma - 1.0);
   fa.tr = s->tr;
   fa.fl = s->fl;
   fa.flux_kind = (int)s->flux;
@@ -596,6 +598,8 @@ VolArgs stage_vol_args(const adg_solver* s, int m) {
   va.tab = s->tab_dev;
   va.gamma = s->opt.gamma;
   va.gammaf = split2(s->opt.gamma);
+  va.gm1 = s->opt.gamma - 1.0;
+  va.gm1f = split2(s->opt.gamma - 1.0);
   va.mode = s->rk2n ? kMode2N : kMode2R;
   va.stage = m;
   va.last = (m == s->stages - 1);
@@ -988,6 +992,8 @@ adg_status adg_step(adg_solver* s, int n_steps) {
         la.m = s->margs;
         la.gamma = s->opt.gamma;
         la.gammaf = split2(s->opt.gamma);
+        la.gm1 = fa.gm1;
+        la.gm1f = fa.gm1f;
         la.ring = s->ring;
         la.fl = s->fl;
         la.face_d = s->pe_face_d;
@@ -1147,6 +1153,8 @@ adg_status adg_rhs(adg_solver* s, const double* u, double* k, int64_t count, int
   va.tab = s->tab_dev;
   va.gamma = s->opt.gamma;
   va.gammaf = split2(s->opt.gamma);
+  va.gm1 = s->opt.gamma - 1.0;
+  va.gm1f = split2(s->opt.gamma - 1.0);
   va.mode = kModeRHS;
   va.w_in = ud;
   va.kout = kd;

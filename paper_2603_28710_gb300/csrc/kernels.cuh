@@ -147,9 +147,8 @@ __device__ __forceinline__ void side_flux(const R (&w)[D + 2], int d, R gamma, R
 // subdomain-face levels and their AT combinations all carry the factor two.
 template <int D, typename R>
 __device__ __forceinline__ void llf_flux(const R (&wm)[D + 2], const R (&wp)[D + 2], int d,
-                                         R gamma, R (&f)[D + 2]) {
+                                         R gamma, R gm1, R (&f)[D + 2]) {
   constexpr int NV = D + 2;
-  const R gm1 = gamma - R(1.0f);
   R fm[NV], fp[NV], sm, sp;
   if constexpr (std::is_same<R, df64>::value) {
     // FP32 pairs: both sides in the two lanes of packed FP32x2 instructions
@@ -564,7 +563,6 @@ __device__ __forceinline__ void vol_body(const VolArgs& A, int tile, unsigned ch
   const S* rin = reinterpret_cast<const S*>(A.r_in);
   const int tid = threadIdx.x;
   bool bulk = false, group2 = false;  // block-uniform
-  bool gave_up = false;               // a bounded wait for the bulk copies ran out
   if constexpr (kStage) {
     // group 1: the stage input (FP64 solution, or the 2R register r into the q slots);
     // group 2: the solution when the input was r, and the 2N register q
@@ -620,9 +618,11 @@ __device__ __forceinline__ void vol_body(const VolArgs& A, int tile, unsigned ch
     if (!bulk) {
       cp_async_wait<1>();
     } else if constexpr (kBulk) {
+      // a wait that runs out flags the results as invalid and waits once more (bounded)
+      // for the copies, so that none is in flight when the block's shared memory is reused
       if (!mbar_wait_bounded(vbar, 0, kWaitLimitCycles)) {
-        gave_up = true;
         atomicOr(faces.err, 2);
+        mbar_wait_bounded(vbar, 0, kWaitLimitCycles);
       }
     }
 #pragma unroll
@@ -642,7 +642,7 @@ __device__ __forceinline__ void vol_body(const VolArgs& A, int tile, unsigned ch
   float4* sF4 = reinterpret_cast<float4*>(smem_raw);  // [EPB][D][NP][ND] (packed sweeps)
   {
     R F[D][NV];
-    euler_flux_all<D, R>(u, Arith<R>::pair(A.gamma, A.gammaf) - R(1.0f), F);
+    euler_flux_all<D, R>(u, Arith<R>::pair(A.gm1, A.gm1f), F);
     if constexpr (PackedSweeps<D, R>::value) {
 #pragma unroll
       for (int d = 0; d < D; ++d)
@@ -736,8 +736,8 @@ __device__ __forceinline__ void vol_body(const VolArgs& A, int tile, unsigned ch
       cp_async_wait<0>();
     } else if constexpr (kBulk) {
       if (group2 && !mbar_wait_bounded(vbar + 1, 0, kWaitLimitCycles)) {
-        gave_up = true;
         atomicOr(faces.err, 2);
+        mbar_wait_bounded(vbar + 1, 0, kWaitLimitCycles);
       }
     }
   }
@@ -766,14 +766,6 @@ __device__ __forceinline__ void vol_body(const VolArgs& A, int tile, unsigned ch
     for (int v = 0; v < NV; ++v) sX[el * SXS + v * ND + node] = xnext[v];
     __syncthreads();
     write_traces<D, N, R, TT, C, SXS>(A.m, A.tab, sX, e0, reinterpret_cast<S*>(A.tr));
-  }
-  if constexpr (kBulk) {
-    // after a wait that ran out (the results are then flagged as invalid): wait once more,
-    // again bounded, for the tile's copies before the block's shared memory is released
-    if (gave_up) {
-      mbar_wait_bounded(vbar, 0, kWaitLimitCycles);
-      if (group2) mbar_wait_bounded(vbar + 1, 0, kWaitLimitCycles);
-    }
   }
 }
 
@@ -819,9 +811,9 @@ __device__ __forceinline__ void face_flux(const FluxArgs& A, int d, int slot, in
                                           R (&f)[D + 2]) {
   using S = typename Arith<R>::S;
   constexpr int NF = IPow<N, D - 1>::value, NV = D + 2;
-  const R gamma = Arith<R>::pair(A.gamma, A.gammaf);
+  const R gamma = Arith<R>::pair(A.gamma, A.gammaf), gm1 = Arith<R>::pair(A.gm1, A.gm1f);
   if (slot < 0) {
-    llf_flux<D, R>(wm, wp, d, gamma, f);
+    llf_flux<D, R>(wm, wp, d, gamma, gm1, f);
     return;
   }
   S* ring = reinterpret_cast<S*>(A.ring);
@@ -846,7 +838,7 @@ __device__ __forceinline__ void face_flux(const FluxArgs& A, int d, int slot, in
   }
   if (kt == 0 || (A.store && !traces)) {
     R fr[NV];
-    llf_flux<D, R>(wm, wp, d, gamma, fr);
+    llf_flux<D, R>(wm, wp, d, gamma, gm1, fr);
     if (A.store && !traces && owner) {
       S* dst = ring + A.head * lvl_stride;
 #pragma unroll
@@ -876,7 +868,7 @@ __device__ __forceinline__ void face_flux(const FluxArgs& A, int d, int slot, in
       R em[NV], ep[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) { em[v] = acc_result(am[v]); ep[v] = acc_result(ap[v]); }
-      llf_flux<D, R>(em, ep, d, gamma, f);
+      llf_flux<D, R>(em, ep, d, gamma, gm1, f);
     } else {
 #pragma unroll
       for (int v = 0; v < NV; ++v) f[v] = acc_result(am[v]);

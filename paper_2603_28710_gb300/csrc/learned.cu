@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(128) learned_apply_kernel(const LearnArgs A) {
   }
   const int d = A.face_d[slot], e = A.face_e[slot];
   R f[NV];
-  llf_flux<D, R>(tr[0], tr[1], d, Arith<R>::pair(A.gamma, A.gammaf), f);
+  llf_flux<D, R>(tr[0], tr[1], d, Arith<R>::pair(A.gamma, A.gammaf), Arith<R>::pair(A.gm1, A.gm1f), f);
   S* fl = reinterpret_cast<S*>(A.fl);
   const int ne = (int)A.m.ne;
 #pragma unroll

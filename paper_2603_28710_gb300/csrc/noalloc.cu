@@ -135,6 +135,7 @@ extern "C" adg_status adg_rhs_noalloc(const adg_mesh* mesh, int degree, double g
   std::memset(&fa, 0, sizeof(fa));
   fa.m = m;
   fa.gamma = gamma;
+  fa.gm1 = gamma - 1.0;
   fa.tr = tr;
   fa.fl = fl;
   fa.pe_mode = 0;
@@ -146,6 +147,7 @@ extern "C" adg_status adg_rhs_noalloc(const adg_mesh* mesh, int degree, double g
   va.m = m;
   va.tab = tab_dev;
   va.gamma = gamma;
+  va.gm1 = gamma - 1.0;
   va.mode = kModeRHS;
   va.w_in = u;
   va.kout = k;
